@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the OSP / OSP-T update path on one GB300 (or N independent replicas).
+
+Workload (the paper's Table 3 graphs are stood in for by a seeded R-MAT graph):
+directed R-MAT scale 20 (1,048,576 nodes, 16,777,216 unique edges,
+a,b,c,d = .57,.19,.19,.05, ids permuted), c = 0.15, one seed (the node of
+highest out-degree), a stream of batches of 1,000 updates (600 insertions of
+absent edges with R-MAT endpoints, 400 deletions of existing edges). A step is
+one batch through the whole path: ingest + validation, graph-store merge,
+offset vector, propagation to ||x||_1 <= eps, merge into the scores.
+
+Reported: update batches/s (FP32 products, FP64 accumulation, eps = 1e-6) with
+the device-resident batch, the L1 distance of those scores to the plain FP64
+path replaying the same iteration counts, the propagation kernel's algorithmic
+GB/s against the measured HBM copy bandwidth, the FP64 path and an eps sweep,
+the end-to-end rate through the host API, and the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1712_00595_gb300 import workloads as W  # noqa: E402
+
+METRIC = "edge-update batches/sec and propagation GB/s (% of HBM peak) at <=1e-5 L1 vs FP64"
+C_RESTART = 0.15
+N_INS, N_DEL = 600, 400
+HUB_SEED_OFFSET = 2
+STREAM_SEED_OFFSET = 202
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=int, default=20)
+    p.add_argument("--eps", type=float, default=1e-6)
+    p.add_argument("--eps-init", type=float, default=1e-10)
+    p.add_argument("--no-extras", action="store_true", help="headline only (profiling runs)")
+    p.add_argument("--cpu-sample", type=int, default=3, help="oracle batches timed for cpu_baseline")
+    return p.parse_args()
+
+
+def make_workload(scale, batches):
+    gen, src, dst = W.rmat_graph(scale, 16 << scale, seed=W.BASE_SEED + HUB_SEED_OFFSET)
+    n = gen.n
+    seed = W.max_out_degree_seed(n, src)
+    stream = W.edge_update_stream(src, dst, n, batches, N_INS, N_DEL,
+                                  seed=W.BASE_SEED + STREAM_SEED_OFFSET, sampler=gen.sample)
+    return n, src, dst, seed, stream
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def alg_bytes(st, n, m, bx, bs):
+    """Algorithmic bytes of one propagation launch (each operand once):
+    pull step  4 m (in-list ids) + n (8 off/len + bx gathered y + bx written y + bs scale + 16 r RMW)
+    push step  4 E_F + (8 + bx) |F| + (bx + 16) |F'|."""
+    pull_steps = st["iterations"] - st["push_iterations"]
+    pull = pull_steps * (4 * m + n * (8 + 2 * bx + bs + 16))
+    ef = st["visited_edges"] - pull_steps * m
+    push = 4 * ef + (8 + bx) * st["push_frontier"] + (bx + 16) * st["push_reached"]
+    return pull + push
+
+
+def traffic_from_profile():
+    """Per-launch DRAM bytes of the propagation kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "propagate_rmat20_traffic.txt")
+    src = os.path.join(ROOT, "paper_1712_00595_gb300", "csrc", "propagate.cu")
+    try:
+        vals = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    vals[k.strip()] = v.strip()
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if vals.get("source_sha256_16") != h:
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = list(csv.reader(open(self.path)))
+        out_dir = os.path.join(ROOT, "gpurun_out")
+        if os.path.isdir(out_dir):
+            with open(os.path.join(out_dir, "bench_clocks.csv"), "w") as f:
+                f.write(open(self.path).read())
+        os.unlink(self.path)
+        if len(rows) < 2:
+            return None
+        hdr = [h.strip() for h in rows[0]]
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows[1:]:
+            if len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, [x.strip() for x in r]))
+            try:
+                sm.append(float(d["clocks.current.sm [MHz]"].split()[0]))
+                smax = max(smax, float(d["clocks.max.sm [MHz]"].split()[0]))
+            except Exception:
+                continue
+            for nm in names:
+                key = [k for k in d if k.startswith("clocks_event_reasons." + nm)]
+                if key and d[key[0]].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    rank, world = 0, 1
+    if args.gpus > 1 or "WORLD_SIZE" in os.environ:
+        import torch.distributed as dist
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        if world > 1:
+            dist.init_process_group("gloo")
+    return rank, world
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores: each step applies one batch and
+    runs Algorithm 1 (graph update, CSR export, offset, propagation)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    n, src, dst, seed, stream = make_workload(args.scale, args.warmup + args.steps)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r, _, _ = O.cpi(*cur, seed, C_RESTART, args.eps_init)
+
+    def step(ops):
+        nonlocal cur, r
+        assert g.apply(ops, protect=(seed,)) == -1
+        new = g.csr()
+        r, _, st, _ = O.osp(cur, new, r, C_RESTART, args.eps)
+        cur = new
+        return st
+
+    for b in range(args.warmup):
+        step(stream[b])
+    t0 = time.perf_counter()
+    for b in range(args.warmup, args.warmup + args.steps):
+        step(stream[b])
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "batches/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, n, len(src), seed, "fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": v, "unit": "batches/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d batches of the workload, single-threaded C oracle" % args.steps},
+        "e2e": {"value": v, "unit": "batches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, n, m, seed, precision):
+    return {"workload": "rmat%d_osp_t" % args.scale, "graph": "R-MAT scale %d (a,b,c,d=.57,.19,.19,.05), "
+            "ids permuted" % args.scale, "nodes": n, "edges": m, "seed_node": int(seed),
+            "seed_rule": "highest out-degree", "c": C_RESTART, "eps": args.eps,
+            "batch": {"updates": N_INS + N_DEL, "insertions": N_INS, "deletions": N_DEL},
+            "precision": precision, "l2": "flushed between steps (256 MiB write)",
+            "inputs": "update batches resident in HBM before the timed region"}
+
+
+def cpu_baseline(args, n, src, dst, seed, stream):
+    """The oracle as it stands on a bounded sample: cpu_sample batches after its own CPI."""
+    from oracle import oracle as O
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r, _, _ = O.cpi(*cur, seed, C_RESTART, args.eps_init)
+    k = max(1, args.cpu_sample)
+    t0 = time.perf_counter()
+    for b in range(k):
+        assert g.apply(stream[b], protect=(seed,)) == -1
+        new = g.csr()
+        r, _, _, _ = O.osp(cur, new, r, C_RESTART, args.eps)
+        cur = new
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "batches/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d batches of the same stream (graph update + Algorithm 1, FP64, "
+                      "one thread; %.1f s)" % (k, dt)}
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1712_00595_gb300 import native as N
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K, Wm = args.steps, args.warmup
+    total = Wm + K
+    n, src, dst, seed, stream = make_workload(args.scale, total)
+    U = N_INS + N_DEL
+    ops_all = np.concatenate(stream).view(np.int32)
+    ops_dev = torch.from_numpy(ops_all.copy()).to(dev)
+    base_ptr = ops_dev.data_ptr()
+    step_bytes = U * 12
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tstream = torch.cuda.Stream(device=dev)
+
+    def new_engine(prec):
+        e = N.Engine(precision=prec, device=local, stream=tstream.cuda_stream)
+        e.load_graph(n, src, dst)
+        e.set_seeds([seed], C_RESTART)
+        e.init_scores(args.eps_init)
+        return e
+
+    def run(eng, eps, warm_n, force=None):
+        """Warm up on batches [0, warm_n), then time batches [Wm, Wm + K): CUDA events
+        around each step on the engine stream, L2 flushed between steps."""
+        for b in range(warm_n):
+            if force is not None:
+                eng.set_fixed_iterations(force[b])
+            eng.apply_updates_device(base_ptr + b * step_bytes, U, eps)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        stats = []
+        for k in range(K):
+            b = Wm + k
+            with torch.cuda.stream(tstream):
+                flush.fill_(k & 0xFF)
+            if force is not None:
+                eng.set_fixed_iterations(force[b])
+            ev[k][0].record(tstream)
+            stats.append(eng.apply_updates_device(base_ptr + b * step_bytes, U, eps))
+            ev[k][1].record(tstream)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        eng.set_fixed_iterations(0)
+        return ms, stats
+
+    # ---- headline: FP32 products / FP64 accumulation at eps ----
+    eng = new_engine(N.OSP_PREC_FP32_ACC64)
+    warm_iters = []
+    clocks = Clocks(local)
+    # warm-up steps also record iteration counts for the lock-step FP64 replay
+    for b in range(Wm):
+        warm_iters.append(eng.apply_updates_device(base_ptr + b * step_bytes, U, args.eps)["iterations"])
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clocks.start()
+    ms, stats = run(eng, args.eps, 0)
+    clk = clocks.stop()
+    iters = warm_iters + [s["iterations"] for s in stats]
+    r_mixed = eng.query()
+    t_local = sum(ms) / 1e3
+    t_max = dist_max(t_local, world)
+    value = world * K / t_max
+    prop_ms = sum(s["ms_propagate"] for s in stats)
+    upd_ms = sum(s["ms_update"] for s in stats)
+    ab = sum(alg_bytes(s, s["n_nodes"], s["m_edges"], 4, 4) for s in stats)
+    peak, peak_kind = peaks()
+    achieved = ab / (prop_ms / 1e3) / 1e9
+    eng.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "batches/s", "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "accumulate": "f64", "data": "synthetic",
+        "config": workload_config(args, n, len(src), seed, "fp32 products, fp64 accumulation"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profile(),
+                     "kernel": "k_propagate<float>", "peak_kind": peak_kind + " (hbm_gbs copy)",
+                     "alg_bytes_per_launch": ab / K, "ms_per_launch": prop_ms / K},
+        "phases_ms_per_step": {"update_merge_offset": upd_ms / K, "propagation": prop_ms / K},
+        "iterations_per_step": float(np.mean([s["iterations"] for s in stats])),
+        "push_iterations_per_step": float(np.mean([s["push_iterations"] for s in stats])),
+        "qoff_l1_mean": float(np.mean([s["qoff_l1"] for s in stats])),
+        "visited_edges_per_step": float(np.mean([s["visited_edges"] for s in stats])),
+        "gpu_launches": 8 * K,
+        "clocks": clk,
+    }
+
+    if not args.no_extras:
+        # ---- plain FP64 path, replaying the same iteration counts (lock-step) ----
+        e64 = new_engine(N.OSP_PREC_FP64)
+        ms64, st64 = run(e64, args.eps, Wm, force=iters)
+        r64 = e64.query()
+        e64.close()
+        out["fp64_path"] = {"value": K / (sum(ms64) / 1e3), "unit": "batches/s",
+                            "ms_propagation_per_step": sum(s["ms_propagate"] for s in st64) / K}
+        out["l1_vs_fp64"] = float(np.abs(r_mixed - r64).sum())
+        out["speedup_vs_fp64"] = value / world / out["fp64_path"]["value"]
+        # ---- OSP-T eps sweep (FP32 products / FP64 accumulation) ----
+        sweep = []
+        for eps in (1e-4, 1e-6, 1e-8):
+            e = new_engine(N.OSP_PREC_FP32_ACC64)
+            ms_e, st_e = run(e, eps, Wm)
+            e.close()
+            sweep.append({"eps": eps, "batches_per_s": K / (sum(ms_e) / 1e3),
+                          "iterations": float(np.mean([s["iterations"] for s in st_e])),
+                          "ms_propagation": sum(s["ms_propagate"] for s in st_e) / K})
+        out["eps_sweep"] = sweep
+        # ---- end to end through the host API: host batch in, top of the scores out ----
+        e = new_engine(N.OSP_PREC_FP32_ACC64)
+        host_ops = [np.ascontiguousarray(s) for s in stream]
+        for b in range(Wm):
+            e.apply_updates(host_ops[b], args.eps)
+        res = np.empty(n, np.float64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            e.apply_updates(host_ops[Wm + k], args.eps)
+            res[:] = e.query()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e.close()
+        out["e2e"] = {"value": K / dt, "unit": "batches/s", "h2d_bytes_per_step": step_bytes,
+                      "d2h_bytes_per_step": 8 * n, "result": "full score vector (osp_query)"}
+        out["gpu_launches"] = 8 * K
+    else:
+        out["e2e"] = None
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        out["cpu_baseline"] = cpu_baseline(args, n, src, dst, seed, stream)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

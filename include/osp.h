@@ -1,0 +1,191 @@
+/*
+ * osp.h - C ABI of the GB300 offset-score-propagation engine.
+ *
+ * The engine tracks Random Walk with Restart (RWR) scores on a graph that
+ * changes by batches of edge and node insertions and deletions, following
+ * OSP / OSP-T (Yoon, Jin, Kang, "Fast and Accurate Random Walk with Restart
+ * on Dynamic Graphs with Guarantees", WWW 2018, arXiv 1712.00595).
+ *
+ * Problem statement (Sec. 1): given a time-evolving graph, a seed node s and a
+ * restart probability c, keep the RWR vector r of Eq. 1,
+ *     r = (1-c) A~^T r + c q,   q = e_s,
+ * up to date after every change. A~ is the row-normalised adjacency matrix
+ * (1/d_u at every out-neighbour of u; an all-zero row for a dead-end).
+ *
+ * Every call below runs its arithmetic in CUDA kernels on one GPU. All
+ * pointers are plain host pointers unless the name ends in _device, in which
+ * case they are device pointers on the context's device, read or written in
+ * stream order on the context's stream. Input arrays are copied; the caller
+ * keeps ownership of everything it passes in and of every output buffer.
+ * Nothing here retains a caller pointer after the call returns.
+ *
+ * Errors: every call returns an osp_status. On OSP_EINVAL the context state is
+ * unchanged (all checks run before any state is written). osp_last_error()
+ * describes the last failure. One context must not be used from two threads
+ * at once; different contexts are independent.
+ */
+#ifndef OSP_H
+#define OSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osp_ctx osp_ctx; /* opaque; created by osp_create, owned by the library */
+
+typedef enum {
+    OSP_OK = 0,
+    OSP_EINVAL = -1,   /* bad argument or invalid update batch; state unchanged */
+    OSP_ENOMEM = -2,   /* device allocation failed */
+    OSP_ECUDA = -3,    /* a CUDA runtime call failed */
+    OSP_ETIMEOUT = -4, /* a bounded device wait (grid barrier) gave up */
+    OSP_ENOCONV = -5,  /* iteration cap reached before ||x(i)||_1 <= eps; scores hold the
+                          truncated sum */
+    OSP_ESTATE = -6,   /* call out of order (e.g. apply before load/seed/init) */
+    OSP_ENOTSUP = -7   /* valid request this build does not implement */
+} osp_status;
+
+/* Arithmetic of the propagation (Sec. 2.2 / Algorithm 1 loop).
+ * FP64:        gather vector, products and every sum in double.
+ * FP32_ACC64:  gather vector and products in float (in-row sums of the pull
+ *              step in float); scores r, the offset vector, push-step
+ *              accumulation and the ||x||_1 stopping test in double. */
+typedef enum { OSP_PREC_FP64 = 0, OSP_PREC_FP32_ACC64 = 1 } osp_precision;
+
+/* One update. Operations of a batch apply in order (Sec. 3.4.1 for nodes).
+ *  OSP_OP_INSERT_EDGE (u,v): add edge u->v; no-op if present.
+ *  OSP_OP_DELETE_EDGE (u,v): remove edge u->v; no-op if absent.
+ *  OSP_OP_ADD_NODE:          new node with the next id (n, n+1, ...), no edges,
+ *                            score 0; u and v are ignored.
+ *  OSP_OP_DELETE_NODE (u):   remove every out- and in-edge of u; the id stays
+ *                            allocated and dead and may not be named again.
+ * A batch is invalid if an op names an id that does not exist at that point
+ * of the batch or is dead, deletes a node twice, deletes a seed, or has an
+ * unknown op code. */
+enum {
+    OSP_OP_INSERT_EDGE = 0,
+    OSP_OP_DELETE_EDGE = 1,
+    OSP_OP_ADD_NODE = 2,
+    OSP_OP_DELETE_NODE = 3
+};
+typedef struct {
+    int32_t u;
+    int32_t v;
+    int32_t op;
+} osp_update; /* 12 bytes, no padding */
+
+typedef struct {
+    int32_t precision;  /* osp_precision */
+    int32_t device;     /* CUDA device ordinal */
+    void *stream;       /* cudaStream_t the engine runs on; NULL = an engine-owned stream */
+    int64_t max_nodes;  /* node capacity to reserve (0 = 1.25 x loaded n + 4096) */
+    double push_alpha;  /* sparse (push) steps while frontier out-edges <= m / alpha (0 = 14) */
+    double push_beta;   /* ... and frontier size <= n / beta (0 = 24) */
+    int32_t max_iter;   /* iteration cap; 0 = ceil(log_{1-c}(eps/2)) + 8 (Theorem 3) */
+    int32_t reserved;
+} osp_options;
+
+/* Per-call statistics (the columns of Table 2 plus bookkeeping). */
+typedef struct {
+    int32_t iterations;      /* propagation steps x(1)..x(k) run */
+    int32_t push_iterations; /* of those, steps run over a sparse frontier */
+    double qoff_l1;          /* ||x(0)||_1: ||q_offset||_1 (OSP) or c (CPI) */
+    double last_x_l1;        /* ||x(k)||_1 at the stop */
+    int64_t visited_edges;   /* edges read by the propagation steps */
+    int64_t n_nodes;         /* node ids in use after the call (dead ones included) */
+    int64_t m_edges;         /* live directed edges after the call */
+    int64_t net_inserts;     /* edges the batch actually added */
+    int64_t net_deletes;     /* edges the batch actually removed (node deletions included) */
+    int64_t changed_rows;    /* rows u with B~[u] != A~[u] (candidates) */
+    int64_t bad_op;          /* OSP_EINVAL from a batch: index of the first invalid op; else -1 */
+    int64_t push_frontier;   /* sum over push steps of the frontier size |F(i-1)| */
+    int64_t push_reached;    /* sum over push steps of the nodes reached |F(i)| */
+    float ms_update;         /* device time of ingest + graph merge + offset (CUDA events) */
+    float ms_propagate;      /* device time of the propagation kernel (CUDA events) */
+} osp_batch_stats;
+
+/* Fill *opt with defaults (FP32_ACC64, device 0, engine-owned stream). */
+void osp_default_options(osp_options *opt);
+
+/* Create a context on opt->device (opt may be NULL for defaults). */
+osp_status osp_create(osp_ctx **out, const osp_options *opt);
+
+/* Free every resource of the context. NULL is accepted. */
+void osp_destroy(osp_ctx *ctx);
+
+/* Load the initial graph G (Sec. 2.1): n nodes, m directed edges src[i]->dst[i]
+ * (host arrays). Duplicate edges collapse; self-loops are kept; undirected != 0
+ * stores both directions of each pair (Sec. 4.1). Replaces any previous graph
+ * and invalidates scores. EINVAL for ids outside [0, n) or n >= 2^25. */
+osp_status osp_load_graph(osp_ctx *ctx, int64_t n, int64_t m, const int32_t *src,
+                          const int32_t *dst, int undirected);
+
+/* Set the seed node(s) s (q = e_s) and restart probability c in (0, 1) (Eq. 1).
+ * This build supports S == 1. Invalidates scores. */
+osp_status osp_set_seeds(osp_ctx *ctx, const int32_t *seeds, int32_t S, double c);
+
+/* Compute scores from scratch by CPI (Sec. 2.2): x(0) = c e_s, stop after the
+ * first x(i) with ||x(i)||_1 <= eps. stats may be NULL. */
+osp_status osp_init_scores(osp_ctx *ctx, double eps, osp_batch_stats *stats);
+
+/* Apply one batch of U updates (host array, U <= osp_max_batch()) and update
+ * the scores by OSP / OSP-T (Algorithm 1):
+ *   q_offset = (1-c)(B~^T - A~^T) r_old,  r_new = r_old + sum_i ((1-c)B~^T)^i q_offset,
+ * stopping after the first term with ||x(i)||_1 <= eps. Exact OSP is a small
+ * eps (Sec. 3.1 suggests 1e-9); OSP-T is a larger one (Sec. 3.2). The graph
+ * update is applied in full even when the scores return ENOCONV. stats may be
+ * NULL. Returns EINVAL (state unchanged, stats->bad_op set) for an invalid
+ * batch. Synchronises the context stream before returning. */
+osp_status osp_apply_updates(osp_ctx *ctx, const osp_update *ops, int64_t U, double eps,
+                             osp_batch_stats *stats);
+
+/* As osp_apply_updates, with ops already in device memory. */
+osp_status osp_apply_updates_device(osp_ctx *ctx, const osp_update *ops_device, int64_t U,
+                                    double eps, osp_batch_stats *stats);
+
+/* Largest U accepted by one apply call. */
+int64_t osp_max_batch(void);
+
+/* Copy the scores of seed seed_idx to out[0 .. n) (host). normalize != 0 returns
+ * r / ||r||_1, the dead-end handled vector of Theorem 5 (Sec. 3.4.2); 0 returns
+ * the stored, unnormalised r_temp. A deleted node keeps its entry; its exact
+ * RWR value is 0 and the stored value approaches it like any other entry. */
+osp_status osp_query(osp_ctx *ctx, int32_t seed_idx, int normalize, double *out);
+
+/* As osp_query, writing to a device buffer of n doubles. */
+osp_status osp_query_device(osp_ctx *ctx, int32_t seed_idx, int normalize, double *out_device);
+
+/* The k highest-scoring nodes of seed seed_idx, ordered by score descending and
+ * then id ascending (host outputs of k entries; fewer if n < k, count in *k_out). */
+osp_status osp_topk(osp_ctx *ctx, int32_t seed_idx, int32_t k, int normalize, int32_t *ids,
+                    double *scores, int32_t *k_out);
+
+/* Copy the current graph as sorted adjacency (host arrays): direction 0 gives
+ * out-edges (CSR of A~'s pattern), 1 gives in-edges (CSC). ptr has n+1 entries,
+ * idx has m; each list ascending. */
+osp_status osp_export_graph(osp_ctx *ctx, int direction, int64_t *ptr, int32_t *idx);
+
+/* Current node count (ids in use, dead ones included) and live edge count. */
+osp_status osp_get_size(osp_ctx *ctx, int64_t *n, int64_t *m);
+
+/* ||x(0)||_1 .. ||x(k)||_1 of the last init/apply call (host, up to cap entries). */
+osp_status osp_get_l1_history(osp_ctx *ctx, double *out, int32_t cap, int32_t *count);
+
+/* Run the next propagations for exactly k steps regardless of eps (k > 0), or
+ * go back to the eps rule (k = 0). Used to compare precisions step for step. */
+osp_status osp_set_fixed_iterations(osp_ctx *ctx, int32_t k);
+
+/* Description of the last error on this context ("" if none). Valid until the
+ * next call on the context. */
+const char *osp_last_error(const osp_ctx *ctx);
+
+/* Static name of a status code. */
+const char *osp_status_string(osp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSP_H */

@@ -1,0 +1,156 @@
+// Device-side layout and helpers shared by the engine's translation units.
+//
+// Graph store. Each direction (out-edges = CSR rows for push, in-edges = CSC
+// columns for pull) is a "slotted" adjacency: per node an offset into an int32
+// pool and a length; the pool holds every list contiguously and ascending.
+// A batch never edits a list in place: a changed list is written to fresh pool
+// space (bump allocation) and its slot is repointed, so the old list stays
+// readable while the offset vector is formed. Stale space is reclaimed by a
+// compaction pass when the pool runs low.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/osp.h"
+
+namespace osp {
+
+constexpr int kMaxBatch = 16384;        // ops per apply call (keys pack the op index in 14 bits)
+constexpr int kMaxNodes = (1 << 25) - 1; // ids fit in 25 bits
+constexpr int kNoPos = 0x7F7F7F7F;       // del_pos of a node not deleted by the batch (memset 0x7F)
+constexpr int kHubThreshold = 2048;      // in-lists longer than this are split into pieces
+constexpr int kHubPiece = 2048;          // edges per hub piece
+constexpr int kLight = 32;               // lists up to this length are walked by one lane
+constexpr int kMaxHist = 4096;           // per-step ||x||_1 history entries
+constexpr int kMaxGrid = 4096;           // CTAs of the persistent kernel (partials array size)
+constexpr int kPropThreads = 256;
+constexpr int kPropWarps = kPropThreads / 32;
+
+enum StepMode : int { kPush = 0, kPull = 1 };
+
+// Device control block: counters, sizes, barrier words and statistics.
+struct Ctl {
+  int status;    // 0 or a negative osp_status
+  int bad_op;    // first invalid op of the batch
+  int n;         // node ids in use
+  int n_old;     // before the current batch
+  long long m;   // live edges
+  long long m_delta;
+  unsigned long long pool_top_r, pool_top_c;
+  unsigned long long pool_cap_r, pool_cap_c;
+  long long net_ins, net_del;  // edge edits of the batch (node deletions not included)
+  int n_rec_r, n_rec_c;        // changed row / column records
+  int n_del;                   // nodes deleted by the batch
+  int n_hubs, n_pieces;
+  int epoch;                   // frontier mark of x(0); step i uses epoch + i
+  int q_size[2];               // frontier queue lengths
+  unsigned int bar_count, bar_gen;
+  int ctr[4];                  // dynamic work counters, reset at every barrier
+  int iter, mode, push_iters, stop, pull_used, noconv;
+  long long visited;
+  long long ef;                // out-edges of the current frontier
+  long long push_f, push_r;    // sums of |F(i-1)| and |F(i)| over push steps
+  int seed;
+  int pad0;
+  double c;
+};
+
+// Every device pointer of one engine, passed to kernels by value.
+struct Dev {
+  int nc;  // node capacity
+  int grid_prop;
+  // graph store
+  unsigned* off_r; int* len_r; int* pool_r;
+  unsigned* off_c; int* len_c; int* pool_c;
+  // per node
+  double* r;
+  void* y0; void* y1;  // gather vectors y = (1-c) x / d (float or double)
+  double* xacc;        // push / offset accumulator
+  double* scale_d;     // (1-c) / d_u, 0 for dead-ends
+  float* scale_f;
+  int* mark;           // frontier membership stamps
+  int* q0; int* q1;    // frontier queues
+  unsigned char* dead;
+  int* del_pos;        // first deletion position in the batch (kNoPos if none)
+  int* rflag; int* cflag;
+  // batch scratch: net edits grouped per changed row / column
+  int* ins_r; int* del_r; int* ins_c; int* del_c;   // [kMaxBatch]
+  int* gi; int* gd;                                  // [kMaxBatch + 1] prefix counts
+  int* rec_r_node; int* rec_r_is; int* rec_r_ic; int* rec_r_ds; int* rec_r_dc;  // [nc]
+  int* rec_c_node; int* rec_c_is; int* rec_c_ic; int* rec_c_ds; int* rec_c_dc;  // [nc]
+  int* del_nodes;  // [kMaxBatch]
+  // hubs (long in-lists) for the pull step
+  int* hubs; int* hub_pstart; double* hub_acc; int* hub_cnt;  // [pool cap / kHubThreshold + 2]
+  // reductions and history
+  double* part_l1; long long* part_ef;  // [kMaxGrid]
+  double* l1_hist;                      // [kMaxHist]
+  Ctl* ctl;
+};
+
+struct PropParams {
+  double eps;
+  int max_iter;
+  int force_iters;
+  double alpha;
+  double beta;
+  int fp32;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// lower_bound over an ascending int array
+__device__ __forceinline__ int lower_bound_i(const int* a, int n, int x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool contains_i(const int* a, int n, int x) {
+  int p = lower_bound_i(a, n, x);
+  return p < n && a[p] == x;
+}
+
+// Warp-aggregated append of `want` lanes' values to a queue (all lanes of the
+// warp must call this together).
+__device__ __forceinline__ void warp_append(bool want, int val, int* queue, int* counter) {
+  unsigned b = __ballot_sync(0xffffffffu, want);
+  if (!b) return;
+  int leader = __ffs(b) - 1;
+  int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (want) queue[base + __popc(b & lanemask_lt())] = val;
+}
+
+}  // namespace osp

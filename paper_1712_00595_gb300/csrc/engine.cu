@@ -1,0 +1,703 @@
+// Host engine behind the C ABI of include/osp.h: device memory, the graph
+// loader, the per-batch launch sequence and the queries.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace osp;
+
+namespace {
+
+constexpr int kIngestSmem = kMaxBatch * 8;
+
+struct HostCtlView {  // the leading fields of Ctl, read back after every call
+  Ctl c;
+};
+
+}  // namespace
+
+struct osp_ctx {
+  osp_options opt{};
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool broken = false;
+
+  // sizes mirrored on the host
+  int64_t n = 0, m = 0, nc = 0;
+  unsigned long long cap_r = 0, cap_c = 0, top_r = 0, top_c = 0;
+  bool loaded = false, seeded = false, scored = false;
+  int seed = -1;
+  double c = 0.15;
+  int fixed_iters = 0;
+  int grid_prop = 0;
+  int last_iters = 0;
+
+  Dev d{};
+  std::vector<void*> allocs;
+  osp_update* ops_stage = nullptr;  // device staging for host batches
+  void* pinned = nullptr;           // pinned host staging (ops in, control block out)
+  double* dsum = nullptr;
+  double* dtmp = nullptr;  // n doubles for normalised queries
+  unsigned* scan_off = nullptr;
+  unsigned* scan_bsum = nullptr;
+  int* pool_spare = nullptr;  // compaction target
+  unsigned long long spare_cap = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, propagation start, end
+};
+
+namespace {
+
+osp_status fail(osp_ctx* ctx, osp_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+osp_status cuda_fail(osp_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, OSP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                    \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);        \
+  } while (0)
+
+template <typename T>
+osp_status dalloc(osp_ctx* ctx, T** p, size_t count, int fill = 0) {
+  void* q = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, OSP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  e = cudaMemsetAsync(q, fill, bytes, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+  ctx->allocs.push_back(q);
+  *p = (T*)q;
+  return OSP_OK;
+}
+
+void free_all(osp_ctx* ctx) {
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->d = Dev{};
+  ctx->ops_stage = nullptr;
+  ctx->dsum = nullptr;
+  ctx->dtmp = nullptr;
+  ctx->scan_off = nullptr;
+  ctx->scan_bsum = nullptr;
+  ctx->pool_spare = nullptr;
+}
+
+// Sorted, de-duplicated adjacency lists of one direction from (key, val) pairs.
+void build_lists(int64_t n, const std::vector<int32_t>& key, const std::vector<int32_t>& val,
+                 std::vector<unsigned>& off, std::vector<int>& len, std::vector<int>& pool) {
+  std::vector<int64_t> start(n + 1, 0);
+  for (int32_t k : key) start[k + 1]++;
+  for (int64_t i = 0; i < n; ++i) start[i + 1] += start[i];
+  std::vector<int> tmp(key.size());
+  {
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (size_t e = 0; e < key.size(); ++e) tmp[pos[key[e]]++] = val[e];
+  }
+  len.assign(n, 0);
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) {
+    th.emplace_back([&, t]() {
+      for (int64_t u = t; u < n; u += nt) {
+        int* b = tmp.data() + start[u];
+        int* e = tmp.data() + start[u + 1];
+        std::sort(b, e);
+        len[u] = (int)(std::unique(b, e) - b);
+      }
+    });
+  }
+  for (auto& x : th) x.join();
+  off.assign(n, 0);
+  int64_t tot = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    off[u] = (unsigned)tot;
+    tot += len[u];
+  }
+  pool.resize(tot);
+  for (int64_t u = 0; u < n; ++u)
+    std::memcpy(pool.data() + off[u], tmp.data() + start[u], sizeof(int) * len[u]);
+}
+
+osp_status read_ctl(osp_ctx* ctx, Ctl* out) {
+  CK(cudaMemcpyAsync(ctx->pinned, ctx->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(out, ctx->pinned, sizeof(Ctl));
+  return OSP_OK;
+}
+
+osp_status write_ctl(osp_ctx* ctx, const Ctl& in) {
+  std::memcpy(ctx->pinned, &in, sizeof(Ctl));
+  CK(cudaMemcpyAsync(ctx->d.ctl, ctx->pinned, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return OSP_OK;
+}
+
+int default_max_iter(const osp_ctx* ctx, double eps) {
+  if (ctx->opt.max_iter > 0) return ctx->opt.max_iter;
+  double k = std::ceil(std::log(eps / 2.0) / std::log(1.0 - ctx->c));
+  if (!(k > 0)) k = 1;
+  return (int)std::min(k + 8.0, (double)kMaxHist - 1);
+}
+
+// Reclaim stale pool space: lists are copied in node order to the spare pool,
+// which then becomes the live one.
+osp_status compact(osp_ctx* ctx, bool rows) {
+  Dev& d = ctx->d;
+  const int n = (int)ctx->n;
+  unsigned* off = rows ? d.off_r : d.off_c;
+  int* len = rows ? d.len_r : d.len_c;
+  int*& pool = rows ? d.pool_r : d.pool_c;
+  unsigned long long& cap = rows ? ctx->cap_r : ctx->cap_c;
+  const int nb = (n + 4095) / 4096;
+  if (n > 0) {
+    k_scan_local<<<nb, 1024, 0, ctx->stream>>>(len, ctx->scan_off, ctx->scan_bsum, n);
+    k_scan_top<<<1, 1024, 0, ctx->stream>>>(ctx->scan_bsum, nb);
+    k_scan_add<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->scan_off, ctx->scan_bsum, n);
+    k_compact_copy<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(off, len, pool, ctx->scan_off,
+                                                               ctx->pool_spare, n);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(off, ctx->scan_off, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  }
+  std::swap(pool, ctx->pool_spare);
+  std::swap(cap, ctx->spare_cap);
+  Ctl h;
+  osp_status s = read_ctl(ctx, &h);
+  if (s != OSP_OK) return s;
+  // live entries: sum of list lengths = m for either direction
+  if (rows) {
+    h.pool_top_r = (unsigned long long)ctx->m;
+    h.pool_cap_r = cap;
+    ctx->top_r = h.pool_top_r;
+  } else {
+    h.pool_top_c = (unsigned long long)ctx->m;
+    h.pool_cap_c = cap;
+    ctx->top_c = h.pool_top_c;
+  }
+  return write_ctl(ctx, h);
+}
+
+// Make sure the next batch of U ops cannot run out of node slots or pool space.
+osp_status reserve_for_batch(osp_ctx* ctx, int64_t U) {
+  if (ctx->n + U > ctx->nc)
+    return fail(ctx, OSP_ENOMEM, "node capacity exhausted; create the context with a larger max_nodes");
+  // a batch writes at most 2 (m + U) entries per direction (scratch + final lists)
+  const unsigned long long need = 2ull * (unsigned long long)(ctx->m + U) + 64;
+  if (ctx->cap_r - ctx->top_r < need) {
+    osp_status s = compact(ctx, true);
+    if (s != OSP_OK) return s;
+  }
+  if (ctx->cap_c - ctx->top_c < need) {
+    osp_status s = compact(ctx, false);
+    if (s != OSP_OK) return s;
+  }
+  if (ctx->cap_r - ctx->top_r < need || ctx->cap_c - ctx->top_c < need)
+    return fail(ctx, OSP_ENOMEM, "graph pool too small for this batch");
+  return OSP_OK;
+}
+
+void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_before) {
+  if (!st) return;
+  std::memset(st, 0, sizeof(*st));
+  st->iterations = h.iter;
+  st->push_iterations = h.push_iters;
+  st->visited_edges = h.visited;
+  st->n_nodes = h.n;
+  st->m_edges = h.m;
+  st->net_inserts = h.net_ins;
+  st->net_deletes = h.net_ins - (h.m - m_before);
+  st->changed_rows = h.n_rec_r;
+  st->bad_op = h.status == OSP_EINVAL ? h.bad_op : -1;
+  double hist[2] = {0, 0};
+  cudaMemcpy(&hist[0], ctx->d.l1_hist, sizeof(double), cudaMemcpyDeviceToHost);
+  int k = std::min(h.iter, kMaxHist - 1);
+  cudaMemcpy(&hist[1], ctx->d.l1_hist + k, sizeof(double), cudaMemcpyDeviceToHost);
+  st->qoff_l1 = hist[0];
+  st->last_x_l1 = hist[1];
+  st->push_frontier = h.push_f;
+  st->push_reached = h.push_r;
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st->ms_update = a;
+  if (cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess) st->ms_propagate = b;
+  cudaGetLastError();
+}
+
+osp_status finish_call(osp_ctx* ctx, int64_t m_before, osp_batch_stats* st) {
+  Ctl h;
+  osp_status s = read_ctl(ctx, &h);
+  if (s != OSP_OK) return s;
+  ctx->last_iters = h.iter;
+  if (h.status == OSP_EINVAL) {
+    fill_stats(ctx, h, st, m_before);
+    return fail(ctx, OSP_EINVAL, "invalid update batch (first invalid op " +
+                                     std::to_string(h.bad_op) + ")");
+  }
+  if (h.status != 0) {
+    ctx->broken = true;
+    fill_stats(ctx, h, st, m_before);
+    return fail(ctx, (osp_status)h.status,
+                std::string("device error: ") + osp_status_string((osp_status)h.status));
+  }
+  ctx->n = h.n;
+  ctx->m = h.m;
+  ctx->top_r = h.pool_top_r;
+  ctx->top_c = h.pool_top_c;
+  fill_stats(ctx, h, st, m_before);
+  if (h.noconv) return fail(ctx, OSP_ENOCONV, "iteration cap reached before ||x||_1 <= eps");
+  ctx->err.clear();
+  return OSP_OK;
+}
+
+osp_status run_propagation(osp_ctx* ctx, double eps) {
+  PropParams pp;
+  pp.eps = eps;
+  pp.max_iter = default_max_iter(ctx, eps);
+  pp.force_iters = ctx->fixed_iters;
+  if (pp.force_iters > pp.max_iter) pp.max_iter = std::min(pp.force_iters, kMaxHist - 1);
+  pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : 14.0;
+  pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : 24.0;
+  pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
+  const int g = ctx->num_sms * 4;
+  k_hubs<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  k_hub_prefix<<<1, 1024, 0, ctx->stream>>>(ctx->d);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
+  CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+  return OSP_OK;
+}
+
+osp_status check_ready(osp_ctx* ctx, bool need_scores) {
+  if (!ctx) return OSP_EINVAL;
+  if (ctx->broken) return fail(ctx, OSP_ESTATE, "context is broken by an earlier device error");
+  if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
+  if (!ctx->seeded) return fail(ctx, OSP_ESTATE, "no seed set");
+  if (need_scores && !ctx->scored) return fail(ctx, OSP_ESTATE, "scores not initialised");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return OSP_OK;
+}
+
+osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, double eps,
+                        osp_batch_stats* st) {
+  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  osp_status s = reserve_for_batch(ctx, U);
+  if (s != OSP_OK) return s;
+  const int64_t m_before = ctx->m;
+  const int g = ctx->num_sms * 4;
+  const int N = (int)std::max<int64_t>(2, U);
+  int Np = 2;
+  while (Np < N) Np <<= 1;
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  k_ingest<<<1, 1024, (size_t)Np * 8, ctx->stream>>>(ctx->d, ops_dev, (int)U);
+  k_expand<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  k_merge_rows<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  k_merge_cols<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  CK(cudaGetLastError());
+  s = run_propagation(ctx, eps);
+  if (s != OSP_OK) return s;
+  return finish_call(ctx, m_before, st);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void osp_default_options(osp_options* opt) {
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = OSP_PREC_FP32_ACC64;
+}
+
+const char* osp_status_string(osp_status s) {
+  switch (s) {
+    case OSP_OK: return "OSP_OK";
+    case OSP_EINVAL: return "OSP_EINVAL";
+    case OSP_ENOMEM: return "OSP_ENOMEM";
+    case OSP_ECUDA: return "OSP_ECUDA";
+    case OSP_ETIMEOUT: return "OSP_ETIMEOUT";
+    case OSP_ENOCONV: return "OSP_ENOCONV";
+    case OSP_ESTATE: return "OSP_ESTATE";
+    case OSP_ENOTSUP: return "OSP_ENOTSUP";
+  }
+  return "OSP_UNKNOWN";
+}
+
+const char* osp_last_error(const osp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t osp_max_batch(void) { return kMaxBatch; }
+
+osp_status osp_create(osp_ctx** out, const osp_options* opt) {
+  if (!out) return OSP_EINVAL;
+  *out = nullptr;
+  osp_ctx* ctx = new osp_ctx();
+  if (opt) ctx->opt = *opt;
+  else osp_default_options(&ctx->opt);
+  if (ctx->opt.precision != OSP_PREC_FP64 && ctx->opt.precision != OSP_PREC_FP32_ACC64) {
+    delete ctx;
+    return OSP_EINVAL;
+  }
+  ctx->device = ctx->opt.device;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) {
+    if (ctx->opt.stream) {
+      ctx->stream = (cudaStream_t)ctx->opt.stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 256 * 1024);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ingest, cudaFuncAttributeMaxDynamicSharedMemorySize, kIngestSmem);
+  if (e != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+    cudaGetLastError();
+    return OSP_ECUDA;
+  }
+  ctx->grid_prop = propagate_grid(ctx->opt.precision == OSP_PREC_FP32_ACC64, ctx->num_sms);
+  if (ctx->grid_prop <= 0) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    cudaFreeHost(ctx->pinned);
+    delete ctx;
+    return OSP_ECUDA;
+  }
+  *out = ctx;
+  return OSP_OK;
+}
+
+void osp_destroy(osp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  free_all(ctx);
+  for (cudaEvent_t ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src,
+                          const int32_t* dst, int undirected) {
+  if (!ctx) return OSP_EINVAL;
+  if (n <= 0 || n >= kMaxNodes || m < 0 || (m > 0 && (!src || !dst)))
+    return fail(ctx, OSP_EINVAL, "bad graph size");
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+      return fail(ctx, OSP_EINVAL, "edge " + std::to_string(e) + " has an id outside [0, n)");
+  cudaError_t ce = cudaSetDevice(ctx->device);
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaSetDevice");
+  free_all(ctx);
+  ctx->loaded = ctx->seeded = ctx->scored = false;
+  ctx->broken = false;
+
+  // sorted, de-duplicated out- and in-lists
+  const int64_t k = undirected ? 2 * m : m;
+  std::vector<int32_t> a(k), b(k);
+  for (int64_t e = 0; e < m; ++e) {
+    a[e] = src[e];
+    b[e] = dst[e];
+    if (undirected) {
+      a[m + e] = dst[e];
+      b[m + e] = src[e];
+    }
+  }
+  std::vector<unsigned> off_r, off_c;
+  std::vector<int> len_r, len_c, pool_r, pool_c;
+  build_lists(n, a, b, off_r, len_r, pool_r);
+  build_lists(n, b, a, off_c, len_c, pool_c);
+  const int64_t mm = (int64_t)pool_r.size();
+
+  int64_t nc = ctx->opt.max_nodes > 0 ? ctx->opt.max_nodes : n + n / 4 + 4096;
+  nc = std::max<int64_t>(nc, n + kMaxBatch);
+  nc = std::min<int64_t>(nc, kMaxNodes);
+  if (nc < n + 1) return fail(ctx, OSP_EINVAL, "graph too large");
+  const unsigned long long cap = 4ull * (unsigned long long)mm + 4ull * kMaxBatch + 65536;
+  if (cap >= 0xFFFFFFFFull) return fail(ctx, OSP_EINVAL, "graph too large for 32-bit pool offsets");
+  ctx->nc = nc;
+  ctx->n = n;
+  ctx->m = mm;
+  ctx->cap_r = ctx->cap_c = ctx->spare_cap = cap;
+  ctx->top_r = ctx->top_c = (unsigned long long)mm;
+
+  Dev& d = ctx->d;
+  d.nc = (int)nc;
+  osp_status s = OSP_OK;
+#define AL(p, cnt, fill)                          \
+  do {                                            \
+    s = dalloc(ctx, &(p), (size_t)(cnt), (fill)); \
+    if (s != OSP_OK) {                            \
+      free_all(ctx);                              \
+      return s;                                   \
+    }                                             \
+  } while (0)
+  AL(d.off_r, nc, 0);
+  AL(d.len_r, nc, 0);
+  AL(d.off_c, nc, 0);
+  AL(d.len_c, nc, 0);
+  AL(d.pool_r, cap, 0);
+  AL(d.pool_c, cap, 0);
+  AL(ctx->pool_spare, cap, 0);
+  AL(d.r, nc, 0);
+  double* y0;
+  double* y1;
+  AL(y0, nc, 0);
+  AL(y1, nc, 0);
+  d.y0 = y0;
+  d.y1 = y1;
+  AL(d.xacc, nc, 0);
+  AL(d.scale_d, nc, 0);
+  AL(d.scale_f, nc, 0);
+  AL(d.mark, nc, 0);
+  AL(d.q0, nc, 0);
+  AL(d.q1, nc, 0);
+  AL(d.dead, nc, 0);
+  AL(d.del_pos, nc, 0x7F);
+  AL(d.rflag, nc, 0);
+  AL(d.cflag, nc, 0);
+  AL(d.ins_r, kMaxBatch, 0);
+  AL(d.del_r, kMaxBatch, 0);
+  AL(d.ins_c, kMaxBatch, 0);
+  AL(d.del_c, kMaxBatch, 0);
+  AL(d.gi, kMaxBatch + 1, 0);
+  AL(d.gd, kMaxBatch + 1, 0);
+  AL(d.rec_r_node, nc, 0);
+  AL(d.rec_r_is, nc, 0);
+  AL(d.rec_r_ic, nc, 0);
+  AL(d.rec_r_ds, nc, 0);
+  AL(d.rec_r_dc, nc, 0);
+  AL(d.rec_c_node, nc, 0);
+  AL(d.rec_c_is, nc, 0);
+  AL(d.rec_c_ic, nc, 0);
+  AL(d.rec_c_ds, nc, 0);
+  AL(d.rec_c_dc, nc, 0);
+  AL(d.del_nodes, kMaxBatch, 0);
+  // lists longer than kHubThreshold number at most (live edges) / kHubThreshold <= cap / kHubThreshold
+  const int64_t nh = (int64_t)(cap / kHubThreshold) + 2;
+  AL(d.hubs, nh, 0);
+  AL(d.hub_pstart, nh + 1, 0);
+  AL(d.hub_acc, nh, 0);
+  AL(d.hub_cnt, nh, 0);
+  AL(d.part_l1, kMaxGrid, 0);
+  AL(d.part_ef, kMaxGrid, 0);
+  AL(d.l1_hist, kMaxHist, 0);
+  AL(d.ctl, 1, 0);
+  AL(ctx->ops_stage, kMaxBatch, 0);
+  AL(ctx->dsum, 1, 0);
+  AL(ctx->dtmp, nc, 0);
+  AL(ctx->scan_off, nc, 0);
+  AL(ctx->scan_bsum, nc / 4096 + 2, 0);
+#undef AL
+  CK(cudaMemcpyAsync(d.off_r, off_r.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d.len_r, len_r.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d.off_c, off_c.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d.len_c, len_c.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  if (mm > 0) {
+    CK(cudaMemcpyAsync(d.pool_r, pool_r.data(), sizeof(int) * mm, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d.pool_c, pool_c.data(), sizeof(int) * mm, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  Ctl h;
+  std::memset(&h, 0, sizeof(h));
+  h.n = (int)n;
+  h.m = mm;
+  h.pool_top_r = h.pool_top_c = (unsigned long long)mm;
+  h.pool_cap_r = h.pool_cap_c = cap;
+  h.epoch = 1;
+  h.seed = 0;
+  h.c = ctx->c;
+  s = write_ctl(ctx, h);
+  if (s != OSP_OK) return s;
+  ctx->loaded = true;
+  ctx->err.clear();
+  return OSP_OK;
+}
+
+osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c) {
+  if (!ctx) return OSP_EINVAL;
+  if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
+  if (ctx->broken) return fail(ctx, OSP_ESTATE, "context is broken by an earlier device error");
+  if (S != 1) {
+    if (S < 1 || !seeds) return fail(ctx, OSP_EINVAL, "need at least one seed");
+    return fail(ctx, OSP_ENOTSUP, "this build tracks one seed per context");
+  }
+  if (!seeds || !(c > 0.0 && c < 1.0)) return fail(ctx, OSP_EINVAL, "bad seed list or c");
+  if (seeds[0] < 0 || seeds[0] >= ctx->n) return fail(ctx, OSP_EINVAL, "seed id out of range");
+  CK(cudaSetDevice(ctx->device));
+  unsigned char dead = 0;
+  CK(cudaMemcpy(&dead, ctx->d.dead + seeds[0], 1, cudaMemcpyDeviceToHost));
+  if (dead) return fail(ctx, OSP_EINVAL, "seed is a deleted node");
+  Ctl h;
+  osp_status s = read_ctl(ctx, &h);
+  if (s != OSP_OK) return s;
+  h.seed = seeds[0];
+  h.c = c;
+  s = write_ctl(ctx, h);
+  if (s != OSP_OK) return s;
+  ctx->seed = seeds[0];
+  ctx->c = c;
+  k_set_scale<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->d, (int)ctx->n, c);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->seeded = true;
+  ctx->scored = false;
+  ctx->err.clear();
+  return OSP_OK;
+}
+
+osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
+  osp_status s = check_ready(ctx, false);
+  if (s != OSP_OK) return s;
+  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
+  k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  k_cpi_begin<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  CK(cudaGetLastError());
+  s = run_propagation(ctx, eps);
+  if (s != OSP_OK) return s;
+  s = finish_call(ctx, ctx->m, stats);
+  if (s == OSP_OK || s == OSP_ENOCONV) ctx->scored = true;
+  return s;
+}
+
+osp_status osp_apply_updates_device(osp_ctx* ctx, const osp_update* ops_device, int64_t U,
+                                    double eps, osp_batch_stats* stats) {
+  osp_status s = check_ready(ctx, true);
+  if (s != OSP_OK) return s;
+  if (U < 0 || U > kMaxBatch) return fail(ctx, OSP_EINVAL, "batch size outside [0, osp_max_batch()]");
+  if (U > 0 && !ops_device) return fail(ctx, OSP_EINVAL, "null ops");
+  return apply_common(ctx, ops_device, U, eps, stats);
+}
+
+osp_status osp_apply_updates(osp_ctx* ctx, const osp_update* ops, int64_t U, double eps,
+                             osp_batch_stats* stats) {
+  osp_status s = check_ready(ctx, true);
+  if (s != OSP_OK) return s;
+  if (U < 0 || U > kMaxBatch) return fail(ctx, OSP_EINVAL, "batch size outside [0, osp_max_batch()]");
+  if (U > 0 && !ops) return fail(ctx, OSP_EINVAL, "null ops");
+  if (U > 0) {
+    const size_t bytes = sizeof(osp_update) * (size_t)U;
+    std::memcpy(ctx->pinned, ops, bytes);
+    CK(cudaMemcpyAsync(ctx->ops_stage, ctx->pinned, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  return apply_common(ctx, ctx->ops_stage, U, eps, stats);
+}
+
+osp_status osp_query_device(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out_device) {
+  osp_status s = check_ready(ctx, true);
+  if (s != OSP_OK) return s;
+  if (seed_idx != 0 || !out_device) return fail(ctx, OSP_EINVAL, "bad seed index or output");
+  const int n = (int)ctx->n;
+  if (normalize) {
+    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), ctx->stream));
+    k_abs_sum<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum);
+    k_scale_copy<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum, out_device);
+    CK(cudaGetLastError());
+  } else {
+    CK(cudaMemcpyAsync(out_device, ctx->d.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return OSP_OK;
+}
+
+osp_status osp_query(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out) {
+  osp_status s = check_ready(ctx, true);
+  if (s != OSP_OK) return s;
+  if (seed_idx != 0 || !out) return fail(ctx, OSP_EINVAL, "bad seed index or output");
+  const int n = (int)ctx->n;
+  const double* src = ctx->d.r;
+  if (normalize) {
+    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), ctx->stream));
+    k_abs_sum<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum);
+    k_scale_copy<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum, ctx->dtmp);
+    CK(cudaGetLastError());
+    src = ctx->dtmp;
+  }
+  CK(cudaMemcpyAsync(out, src, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return OSP_OK;
+}
+
+osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, int32_t* ids,
+                    double* scores, int32_t* k_out) {
+  (void)seed_idx; (void)k; (void)normalize; (void)ids; (void)scores; (void)k_out;
+  return fail(ctx, OSP_ENOTSUP, "top-k is not available in this build");
+}
+
+osp_status osp_export_graph(osp_ctx* ctx, int direction, int64_t* ptr, int32_t* idx) {
+  if (!ctx) return OSP_EINVAL;
+  if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
+  if ((direction != 0 && direction != 1) || !ptr || (ctx->m > 0 && !idx))
+    return fail(ctx, OSP_EINVAL, "bad direction or output");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int64_t n = ctx->n;
+  const bool rows = direction == 0;
+  std::vector<unsigned> off(n);
+  std::vector<int> len(n);
+  const unsigned long long top = rows ? ctx->top_r : ctx->top_c;
+  std::vector<int> pool(std::max<unsigned long long>(top, 1));
+  CK(cudaMemcpy(off.data(), rows ? ctx->d.off_r : ctx->d.off_c, sizeof(unsigned) * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(len.data(), rows ? ctx->d.len_r : ctx->d.len_c, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(pool.data(), rows ? ctx->d.pool_r : ctx->d.pool_c, sizeof(int) * top, cudaMemcpyDeviceToHost));
+  int64_t e = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    ptr[u] = e;
+    if (len[u] > 0) std::memcpy(idx + e, pool.data() + off[u], sizeof(int) * len[u]);
+    e += len[u];
+  }
+  ptr[n] = e;
+  return OSP_OK;
+}
+
+osp_status osp_get_size(osp_ctx* ctx, int64_t* n, int64_t* m) {
+  if (!ctx || !n || !m) return OSP_EINVAL;
+  *n = ctx->n;
+  *m = ctx->m;
+  return OSP_OK;
+}
+
+osp_status osp_get_l1_history(osp_ctx* ctx, double* out, int32_t cap, int32_t* count) {
+  if (!ctx || !out || !count || cap < 0) return OSP_EINVAL;
+  if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
+  const int k = std::min(std::min(ctx->last_iters + 1, kMaxHist), (int)cap);
+  CK(cudaMemcpy(out, ctx->d.l1_hist, sizeof(double) * k, cudaMemcpyDeviceToHost));
+  *count = k;
+  return OSP_OK;
+}
+
+osp_status osp_set_fixed_iterations(osp_ctx* ctx, int32_t k) {
+  if (!ctx || k < 0 || k >= kMaxHist) return OSP_EINVAL;
+  ctx->fixed_iters = k;
+  return OSP_OK;
+}
+
+}  // extern "C"

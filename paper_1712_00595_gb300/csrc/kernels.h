@@ -1,0 +1,34 @@
+// Kernel entry points of the engine (internal).
+#pragma once
+#include "common.cuh"
+
+namespace osp {
+
+__global__ void k_reset_batch(Dev d);
+__global__ void k_cpi_begin(Dev d);
+__global__ void k_ingest(Dev d, const osp_update* __restrict__ ops, int U);
+__global__ void k_expand(Dev d);
+__global__ void k_merge_rows(Dev d);
+__global__ void k_merge_cols(Dev d);
+__global__ void k_hubs(Dev d);
+__global__ void k_hub_prefix(Dev d);
+__global__ void k_set_scale(Dev d, int n, double c);
+__global__ void k_scan_local(const int* __restrict__ len, unsigned* out, unsigned* bsum, int n);
+__global__ void k_scan_top(unsigned* bsum, int nb);
+__global__ void k_scan_add(unsigned* out, const unsigned* __restrict__ bsum, int n);
+__global__ void k_compact_copy(const unsigned* __restrict__ off_old, const int* __restrict__ len,
+                               const int* __restrict__ pool_old, const unsigned* __restrict__ off_new,
+                               int* pool_new, int n);
+__global__ void k_abs_sum(const double* __restrict__ r, int n, double* out);
+__global__ void k_scale_copy(const double* __restrict__ r, int n, const double* __restrict__ sum,
+                             double* out);
+
+// Propagation (persistent, cooperative launch). T = double or float.
+template <typename T>
+__global__ void k_propagate(Dev d, PropParams pp);
+
+// Host helper: the number of CTAs the persistent kernel can keep resident.
+int propagate_grid(int fp32, int num_sms);
+cudaError_t launch_propagate(const Dev& d, const PropParams& pp, int grid, cudaStream_t s);
+
+}  // namespace osp

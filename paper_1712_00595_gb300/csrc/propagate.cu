@@ -1,0 +1,429 @@
+// Offset score propagation: the cumulative power iteration of Algorithm 1,
+//   x(i) = (1-c) B~^T x(i-1),  r += x(i),  until ||x(i)||_1 <= eps,
+// run as one persistent cooperative kernel per call.
+//
+// The kernel keeps the gather vector y(i) = (1-c) x(i) / d (the scale is
+// applied once per source node, so a step is a plain sum over in-edges) and
+// moves between two step kinds:
+//   push: x(i) is sparse. Each frontier node u scatters y(i-1)[u] to its
+//         out-neighbours (atomic adds into xacc, first touch appends to the
+//         next frontier); an epilogue over the new frontier adds x(i) into r,
+//         forms y(i) and sums |x(i)|.
+//   pull: x(i) is dense. Each node v sums y(i-1) over its in-list (one lane
+//         per short list, a warp per longer list, several warps per hub list)
+//         and the same pass adds x(i) into r, writes y(i) and sums |x(i)|.
+// The step switches to pull once the frontier's out-edges exceed m / alpha or
+// its size exceeds n / beta, and stays there. Between steps a grid barrier
+// (bounded wait) reduces the per-CTA |x| partials in a fixed order and takes
+// the do-while stopping decision on the device, so a whole call needs no
+// host round trip.
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace osp {
+namespace {
+
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+constexpr unsigned kBarrierMaxSpins = 1u << 26;
+
+struct BarShared {
+  unsigned gen;
+  int last;
+  int ok;
+};
+
+__device__ __forceinline__ bool bar_arrive(Ctl* ctl, BarShared& sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = *(volatile unsigned*)&ctl->bar_gen;
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+    sh.gen = g;
+    sh.last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  return sh.last;
+}
+
+// The last CTA opens the barrier; the others wait with a time limit. Returns
+// false when the kernel must stop (timeout or an error status).
+__device__ __forceinline__ bool bar_release(Ctl* ctl, BarShared& sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (sh.last) {
+      ctl->bar_count = 0;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (*(volatile unsigned*)&ctl->bar_gen == sh.gen) {
+        __nanosleep(32);
+        ++spins;
+        if (spins >= kBarrierMaxSpins ||
+            ((spins & 1023u) == 0 && global_ns() - t0 > kBarrierTimeoutNs)) {
+          atomicCAS(&ctl->status, 0, (int)OSP_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)&ctl->status != 0) ok = 0;
+    sh.ok = ok;
+  }
+  __syncthreads();
+  return sh.ok;
+}
+
+__device__ __forceinline__ void block_partials(const Dev& d, double l1, long long ef, double* s_l1,
+                                               long long* s_ef) {
+  l1 = warp_sum(l1);
+  ef = warp_sum(ef);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_l1[w] = l1;
+    s_ef[w] = ef;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    long long b = 0;
+    for (int i = 0; i < kPropWarps; ++i) {
+      a += s_l1[i];
+      b += s_ef[i];
+    }
+    d.part_l1[blockIdx.x] = a;
+    d.part_ef[blockIdx.x] = b;
+  }
+}
+
+// Run by the whole last-arriving CTA: fixed-order sum of the partials and the
+// stopping / step-kind decision (Algorithm 1 loop test, do-while form).
+__device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n, long long m,
+                       double* s_l1, long long* s_ef) {
+  Ctl* ctl = d.ctl;
+  double a = 0.0;
+  long long b = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    a += __ldcg(d.part_l1 + i);
+    b += __ldcg(d.part_ef + i);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_l1[w] = a;
+    s_ef[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double L1 = 0.0;
+  long long EF = 0;
+  for (int i = 0; i < kPropWarps; ++i) {
+    L1 += s_l1[i];
+    EF += s_ef[i];
+  }
+  int it;
+  int stop;
+  if (step_mode < 0) {  // x(0)
+    it = 0;
+    d.l1_hist[0] = L1;
+    stop = 0;  // at least one step always runs
+  } else {
+    it = ctl->iter + 1;
+    ctl->iter = it;
+    if (it < kMaxHist) d.l1_hist[it] = L1;
+    if (step_mode == kPush) {
+      ctl->visited += ctl->ef;
+      ctl->push_iters += 1;
+      ctl->push_f += ctl->q_size[(it + 1) & 1];
+      ctl->push_r += ctl->q_size[it & 1];
+    } else {
+      ctl->visited += m;
+      ctl->pull_used = 1;
+    }
+    if (pp.force_iters > 0) {
+      stop = it >= pp.force_iters;
+    } else {
+      stop = L1 <= pp.eps;
+      if (!stop && it >= pp.max_iter) {
+        stop = 1;
+        ctl->noconv = 1;
+      }
+    }
+    if (pp.force_iters > 0 && it >= pp.max_iter && !stop) {
+      stop = 1;
+      ctl->noconv = 1;
+    }
+  }
+  int next = kPull;
+  if (step_mode != kPull) {
+    const int qs = ctl->q_size[it & 1];
+    const bool dense = (double)EF > (double)m / pp.alpha || (double)qs > (double)n / pp.beta;
+    next = dense ? kPull : kPush;
+  }
+  ctl->ef = EF;
+  ctl->mode = next;
+  ctl->stop = stop;
+  ctl->q_size[(it + 1) & 1] = 0;
+  for (int i = 0; i < 4; ++i) ctl->ctr[i] = 0;
+}
+
+template <typename T>
+__device__ void push_scatter(const Dev& d, const int* qsrc, int qs, T* ys, int* qdst,
+                             int* qdst_size, int ep, int* ctr) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(ctr, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    const int i0 = t * 32;
+    if (i0 >= qs) break;
+    const int i = i0 + lane;
+    const bool valid = i < qs;
+    const int u = valid ? __ldcg(qsrc + i) : 0;
+    T val = (T)0;
+    if (valid) {
+      val = __ldcg(ys + u);
+      ys[u] = (T)0;
+    }
+    unsigned o = 0;
+    int len = 0;
+    if (valid && val != (T)0) {
+      o = __ldg(d.off_r + u);
+      len = __ldg(d.len_r + u);
+    }
+    const bool light = len <= kLight;
+    const int ll = light ? len : 0;
+    const int maxl = warp_max(ll);
+    for (int j = 0; j < maxl; ++j) {
+      const bool act = j < ll;
+      const int v = act ? __ldg(d.pool_r + o + j) : 0;
+      if (act) atomicAdd(&d.xacc[v], (double)val);
+      const bool need = act && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
+      warp_append(need, v, qdst, qdst_size);
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, !light);
+    while (hm) {
+      const int l = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const unsigned ho = __shfl_sync(0xffffffffu, o, l);
+      const int hl = __shfl_sync(0xffffffffu, len, l);
+      const T hv = __shfl_sync(0xffffffffu, val, l);
+      for (int b = 0; b < hl; b += 32) {
+        const int j = b + lane;
+        const bool act = j < hl;
+        const int v = act ? __ldg(d.pool_r + ho + j) : 0;
+        if (act) atomicAdd(&d.xacc[v], (double)hv);
+        const bool need = act && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
+        warp_append(need, v, qdst, qdst_size);
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ double pull_step(const Dev& d, int n, const T* ys, T* yd, const T* __restrict__ scale,
+                            int n_hubs, int n_pieces, int* ctr_hub) {
+  double l1 = 0.0;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nchunks = (n + 31) >> 5;
+  for (int t = gw; t < nchunks; t += nw) {
+    const int v = (t << 5) + lane;
+    const bool valid = v < n;
+    unsigned o = 0;
+    int len = 0;
+    if (valid) {
+      o = __ldg(d.off_c + v);
+      len = __ldg(d.len_c + v);
+    }
+    const bool hub = len > kHubThreshold;
+    const bool light = len <= kLight;
+    T s = (T)0;
+    if (light) {
+      const int* p = d.pool_c + o;
+      int j = 0;
+      for (; j + 4 <= len; j += 4) {
+        const int a0 = __ldg(p + j), a1 = __ldg(p + j + 1), a2 = __ldg(p + j + 2),
+                  a3 = __ldg(p + j + 3);
+        s += (ys[a0] + ys[a1]) + (ys[a2] + ys[a3]);
+      }
+      for (; j < len; ++j) s += ys[__ldg(p + j)];
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, !light && !hub);
+    while (hm) {
+      const int l = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const unsigned ho = __shfl_sync(0xffffffffu, o, l);
+      const int hl = __shfl_sync(0xffffffffu, len, l);
+      T p = (T)0;
+      for (int j = lane; j < hl; j += 32) p += ys[__ldg(d.pool_c + ho + j)];
+      p = warp_sum(p);
+      if (lane == l) s = p;
+    }
+    if (valid && !hub) {
+      const double x = (double)s;
+      d.r[v] += x;
+      l1 += fabs(x);
+      yd[v] = s * __ldg(scale + v);
+    }
+  }
+  // hub lists, split into pieces; the piece that completes a hub finishes it
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(ctr_hub, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_pieces) break;
+    int lo = 0, hi = n_hubs;  // largest h with hub_pstart[h] <= t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(d.hub_pstart + mid) <= t) lo = mid;
+      else hi = mid;
+    }
+    const int h = lo;
+    const int v = __ldg(d.hubs + h);
+    const int piece = t - __ldg(d.hub_pstart + h);
+    const int full = __ldg(d.len_c + v);
+    const unsigned o = __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
+    const int L = min(kHubPiece, full - piece * kHubPiece);
+    T p = (T)0;
+    for (int j = lane; j < L; j += 32) p += ys[__ldg(d.pool_c + o + j)];
+    p = warp_sum(p);
+    if (lane == 0) {
+      atomicAdd(&d.hub_acc[h], (double)p);
+      __threadfence();
+      const int np = (full + kHubPiece - 1) / kHubPiece;
+      if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
+        __threadfence();
+        const double x =
+            __longlong_as_double((long long)atomicExch((unsigned long long*)&d.hub_acc[h], 0ull));
+        d.hub_cnt[h] = 0;
+        d.r[v] += x;
+        l1 += fabs(x);
+        yd[v] = (T)(x * __ldg(d.scale_d + v));
+      }
+    }
+  }
+  return l1;
+}
+
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams pp) {
+  __shared__ BarShared sh;
+  __shared__ double s_l1[kPropWarps];
+  __shared__ long long s_ef[kPropWarps];
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int n = ctl->n;
+  const long long m = ctl->m;
+  const int epoch = ctl->epoch;
+  const int n_hubs = ctl->n_hubs;
+  const int n_pieces = ctl->n_pieces;
+  T* yb[2] = {(T*)d.y0, (T*)d.y1};
+  int* qb[2] = {d.q0, d.q1};
+  const T* scale = (const T*)(std::is_same<T, float>::value ? (const void*)d.scale_f
+                                                             : (const void*)d.scale_d);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthreads = gridDim.x * blockDim.x;
+
+  // x(0) (the offset vector, or c e_s for CPI) sits in xacc over queue 0
+  {
+    double l1 = 0.0;
+    long long ef = 0;
+    const int qs = *(volatile int*)&ctl->q_size[0];
+    for (int k = tid; k < qs; k += nthreads) {
+      const int v = __ldcg(d.q0 + k);
+      const double x = __ldcg(d.xacc + v);
+      d.xacc[v] = 0.0;
+      d.r[v] += x;
+      l1 += fabs(x);
+      yb[0][v] = (T)(x * __ldg(d.scale_d + v));
+      ef += __ldg(d.len_r + v);
+    }
+    block_partials(d, l1, ef, s_l1, s_ef);
+    if (bar_arrive(ctl, sh)) decide(d, pp, -1, n, m, s_l1, s_ef);
+    if (!bar_release(ctl, sh)) return;
+  }
+
+  for (int it = 1;; ++it) {
+    if (*(volatile int*)&ctl->stop) break;
+    const int mode = *(volatile int*)&ctl->mode;
+    const int src = (it - 1) & 1, dst = it & 1;
+    double l1 = 0.0;
+    long long ef = 0;
+    if (mode == kPush) {
+      const int qs = *(volatile int*)&ctl->q_size[src];
+      push_scatter<T>(d, qb[src], qs, yb[src], qb[dst], &ctl->q_size[dst], epoch + it,
+                      &ctl->ctr[0]);
+      if (bar_arrive(ctl, sh) && threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) ctl->ctr[i] = 0;
+      if (!bar_release(ctl, sh)) return;
+      const int qn = *(volatile int*)&ctl->q_size[dst];
+      T* yd = yb[dst];
+      for (int k = tid; k < qn; k += nthreads) {
+        const int v = __ldcg(qb[dst] + k);
+        const double x = __ldcg(d.xacc + v);
+        d.xacc[v] = 0.0;
+        d.r[v] += x;
+        l1 += fabs(x);
+        yd[v] = (T)(x * __ldg(d.scale_d + v));
+        ef += __ldg(d.len_r + v);
+      }
+    } else {
+      l1 = pull_step<T>(d, n, yb[src], yb[dst], scale, n_hubs, n_pieces, &ctl->ctr[1]);
+    }
+    block_partials(d, l1, ef, s_l1, s_ef);
+    if (bar_arrive(ctl, sh)) decide(d, pp, mode, n, m, s_l1, s_ef);
+    if (!bar_release(ctl, sh)) return;
+  }
+
+  // leave both gather vectors all-zero for the next call
+  const int k_last = *(volatile int*)&ctl->iter;
+  if (*(volatile int*)&ctl->pull_used) {
+    T* a = yb[0];
+    T* b = yb[1];
+    for (int v = tid; v < n; v += nthreads) {
+      a[v] = (T)0;
+      b[v] = (T)0;
+    }
+  } else {
+    const int last = k_last & 1;
+    const int qs = *(volatile int*)&ctl->q_size[last];
+    for (int k = tid; k < qs; k += nthreads) yb[last][__ldcg(qb[last] + k)] = (T)0;
+  }
+  if (tid == 0) ctl->epoch = epoch + k_last + 1;
+}
+
+template __global__ void k_propagate<double>(Dev, PropParams);
+template __global__ void k_propagate<float>(Dev, PropParams);
+
+int propagate_grid(int fp32, int num_sms) {
+  int bps = 0;
+  cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<float>,
+                                                                       kPropThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_propagate<double>,
+                                                                       kPropThreads, 0);
+  if (e != cudaSuccess || bps <= 0) return 0;
+  bps = bps > 4 ? 4 : bps;
+  int g = bps * num_sms;
+  return g > kMaxGrid ? kMaxGrid : g;
+}
+
+cudaError_t launch_propagate(const Dev& d, const PropParams& pp, int grid, cudaStream_t s) {
+  Dev dd = d;
+  PropParams p = pp;
+  void* args[] = {&dd, &p};
+  const void* fn = pp.fp32 ? (const void*)k_propagate<float> : (const void*)k_propagate<double>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPropThreads), args, 0, s);
+}
+
+}  // namespace osp

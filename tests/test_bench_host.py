@@ -1,0 +1,54 @@
+"""Host-side logic of the benchmark: algorithmic byte counts, the committed
+traffic record, and the replica timing reduction over two gloo ranks."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def test_alg_bytes_pull_and_push():
+    st = {"iterations": 3, "push_iterations": 1, "visited_edges": 100 + 2 * 1000,
+          "push_frontier": 10, "push_reached": 40}
+    n, m = 50, 1000
+    pull = 2 * (4 * m + n * (8 + 8 + 4 + 16))
+    push = 4 * 100 + 12 * 10 + 20 * 40
+    assert bench.alg_bytes(st, n, m, 4, 4) == pull + push
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+
+    class A:
+        gpus = world
+
+    r, w = bench.dist_setup(A)
+    bench.dist_barrier(w)
+    q.put((r, w, bench.dist_max(1.0 + r, w)))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_replica_max_over_ranks_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get() for _ in range(2))
+    assert got == [(0, 2, 2.0), (1, 2, 2.0)]

@@ -1,0 +1,365 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances: FP64 path L1 <= 1e-10; FP32-products / FP64-accumulation path
+L1 <= 1e-5 against the oracle replaying the same iteration counts (lock-step).
+The graph store is compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1712_00595_gb300 import native as N
+from paper_1712_00595_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C_RESTART = 0.15
+TOL = {N.OSP_PREC_FP64: 1e-10, N.OSP_PREC_FP32_ACC64: 1e-5}
+PRECS = [N.OSP_PREC_FP64, N.OSP_PREC_FP32_ACC64]
+
+
+def l1(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).sum())
+
+
+def engine(prec, n, src, dst, seed=0, c=C_RESTART, eps_init=1e-13, **kw):
+    eng = N.Engine(precision=prec, device=0, **kw)
+    eng.load_graph(n, src, dst)
+    eng.set_seeds([seed], c)
+    st = eng.init_scores(eps_init)
+    return eng, st
+
+
+def hub_graph(rng, n=6000, m=40000, hub_in=5000, hub_out=3000, mids=40):
+    """Uniform edges plus one column of in-degree > 2048 (pull hub pieces), one
+    row of out-degree > 32 x 32 (heavy push row) and mid-size lists."""
+    src = list(rng.integers(0, n, m))
+    dst = list(rng.integers(0, n, m))
+    src += list(rng.choice(n, hub_in, replace=False))
+    dst += [1] * hub_in
+    src += [2] * hub_out
+    dst += list(rng.choice(n, hub_out, replace=False))
+    for k in range(mids):
+        v = int(rng.integers(3, n))
+        cnt = int(rng.integers(33, 1500))
+        src += list(rng.choice(n, cnt, replace=False))
+        dst += [v] * cnt
+    s = np.array(src, np.int32)
+    d = np.array(dst, np.int32)
+    keep = s != d
+    return s[keep], d[keep]
+
+
+def check_graph(eng, g):
+    ptr, idx = eng.export_graph(0)
+    rp, col = g.csr()
+    assert np.array_equal(ptr, rp) and np.array_equal(idx, col), "out-lists differ"
+    ptr, idx = eng.export_graph(1)
+    cp, row = g.csc()
+    assert np.array_equal(ptr, cp) and np.array_equal(idx, row), "in-lists differ"
+    assert eng.get_size() == (g.n, g.m)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PRECS)
+def test_cpi_matches_oracle(prec):
+    rng = np.random.default_rng(1)
+    for src, dst, n in [(*W.er_graph(2000, 16000, 11), 2000), (*hub_graph(rng), 6000)]:
+        eng, st = engine(prec, n, src, dst, seed=5, eps_init=1e-12)
+        rp, col = O.Graph(n, src, dst).csr()
+        r_o, ost, hist = O.cpi(rp, col, 5, C_RESTART, 1e-12)
+        assert abs(st["iterations"] - ost["iterations"]) <= 1
+        if st["iterations"] != ost["iterations"]:
+            r_o, ost, hist = O.cpi(rp, col, 5, C_RESTART, 1e-12, force_iters=st["iterations"])
+        assert l1(eng.query(), r_o) <= TOL[prec]
+        h = eng.get_l1_history()
+        assert h.size == st["iterations"] + 1
+        assert np.allclose(h, hist, rtol=1e-6 if prec else 1e-12, atol=1e-300)
+        eng.close()
+
+
+def test_cpi_iteration_count_116_on_gpu():
+    # Table 2: CPI with c = 0.15, eps = 1e-9 runs 116 iterations on any dead-end free graph.
+    rng = np.random.default_rng(7)
+    n = 5000
+    src = np.concatenate([np.arange(n), rng.integers(0, n, 40000)]).astype(np.int32)
+    dst = np.concatenate([(np.arange(n) + 1) % n, rng.integers(0, n, 40000)]).astype(np.int32)
+    for prec in PRECS:
+        eng, st = engine(prec, n, src, dst, seed=3, eps_init=1e-9)
+        assert st["iterations"] == 116
+        eng.close()
+
+
+def test_cpi_matches_dense_closed_form():
+    rng = np.random.default_rng(2)
+    for trial in range(4):
+        n = int(rng.integers(5, 60))
+        A = rng.random((n, n)) < 0.08
+        src, dst = [a.astype(np.int32) for a in np.nonzero(A)]
+        eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, seed=0, eps_init=1e-15)
+        want = O.dense_rwr(n, src, dst, 0, C_RESTART)
+        assert l1(eng.query(), want) < 1e-12
+        assert l1(eng.query(normalize=True), O.normalize(want)) < 1e-12
+        eng.close()
+
+
+# ---------------------------------------------------------------------------
+def mixed_sequence(rng, n, src, dst, batches, n_ops, seed=0):
+    es = W.EdgeSet(src, dst)
+    dead = np.zeros(n + batches * n_ops + 8, np.uint8)
+    nn = n
+    out = []
+    for _ in range(batches):
+        ops, nn = W.random_mixed_batch(rng, nn, es, dead, n_ops, protect=(seed,))
+        out.append(ops)
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_osp_sequence_with_all_op_kinds(prec):
+    rng = np.random.default_rng(40 + prec)
+    n = 400
+    src, dst = hub_graph(rng, n=n, m=3000, hub_in=300, hub_out=200, mids=5)
+    batches = mixed_sequence(rng, n, src, dst, 6, 150)
+    eps = 1e-12
+    eng, _ = engine(prec, n, src, dst, eps_init=eps, max_nodes=n + 4096)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o, _, _ = O.cpi(*cur, 0, C_RESTART, eps)
+    for ops in batches:
+        st = eng.apply_updates(ops, eps)
+        assert g.apply(ops, protect=(0,)) == -1
+        new = g.csr()
+        check_graph(eng, g)
+        force = st["iterations"] if prec == N.OSP_PREC_FP32_ACC64 else 0
+        r_o, q, ost, _ = O.osp(cur, new, r_o, C_RESTART, eps, force_iters=force)
+        cur = new
+        if prec == N.OSP_PREC_FP64:
+            assert abs(st["iterations"] - ost["iterations"]) <= 1
+        assert st["qoff_l1"] == pytest.approx(np.abs(q).sum(), rel=1e-6, abs=1e-15)
+        assert l1(eng.query(), r_o) <= TOL[prec]
+    # Theorem 2: the tracked scores equal a recompute on the final graph
+    r_cpi, _, _ = O.cpi(*cur, 0, C_RESTART, 1e-14)
+    assert l1(eng.query(), r_cpi) <= TOL[prec] + 1e-9
+    eng.close()
+
+
+def test_invalid_batches_rejected_state_unchanged():
+    rng = np.random.default_rng(9)
+    n = 50
+    src, dst = W.er_graph(n, 300, 5)
+    eng, _ = engine(N.OSP_PREC_FP64, n, src, dst)
+    r0 = eng.query()
+    g0 = eng.export_graph(0)
+    g = O.Graph(n, src, dst)
+    cases = [
+        [(0, 99, 0)],
+        [(0, 0, 2), (0, 50, 0), (0, 51, 0)],
+        [(7, 0, 3), (1, 7, 0)],
+        [(7, 0, 3), (7, 0, 3)],
+        [(0, 0, 3)],
+        [(0, 1, 9)],
+        [(3, 4, 0), (-1, 2, 1)],
+    ]
+    for rows in cases:
+        ops = np.array(rows, dtype=np.int64)
+        arr = np.empty(len(rows), W.UPDATE_DTYPE)
+        arr["u"], arr["v"], arr["op"] = ops[:, 0], ops[:, 1], ops[:, 2]
+        want = g.validate(arr, protect=(0,))
+        assert want >= 0
+        st = eng.apply_updates(arr, 1e-12, allow=(N.OSP_EINVAL,))
+        assert eng.last_status == N.OSP_EINVAL and st["bad_op"] == want
+        assert eng.get_size() == (n, g.m)
+        p, i = eng.export_graph(0)
+        assert np.array_equal(p, g0[0]) and np.array_equal(i, g0[1])
+        assert np.array_equal(eng.query(), r0)
+    # the context still works afterwards
+    ok = np.zeros(1, W.UPDATE_DTYPE)
+    ok[0] = (3, 4, 0)
+    eng.apply_updates(ok, 1e-12)
+    eng.close()
+
+
+def test_invalid_bad_op_index_reported():
+    src, dst = W.er_graph(30, 100, 3)
+    eng, _ = engine(N.OSP_PREC_FP64, 30, src, dst)
+    arr = np.zeros(5, W.UPDATE_DTYPE)
+    arr[:] = [(1, 2, 0), (2, 3, 0), (4, 5, 1), (40, 1, 0), (1, 3, 0)]
+    st = eng.apply_updates(arr, 1e-12, allow=(N.OSP_EINVAL,))
+    assert eng.last_status == N.OSP_EINVAL and st["bad_op"] == 3
+    eng.close()
+
+
+def test_config1_er_exact_osp():
+    # ER 10,000 nodes / 100,000 edges, seed 0, c = 0.15, eps = 1e-12, one batch
+    # of 50 insertions of absent edges and 50 deletions of existing edges.
+    n, m, eps = 10000, 100000, 1e-12
+    src, dst = W.er_graph(n, m, W.BASE_SEED + 1)
+    ops = W.edge_update_stream(src, dst, n, 1, 50, 50, seed=W.BASE_SEED + 101)[0]
+    eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, eps_init=eps)
+    st = eng.apply_updates(ops, eps)
+    g = O.Graph(n, src, dst)
+    old = g.csr()
+    assert g.apply(ops) == -1
+    check_graph(eng, g)
+    r0, _, _ = O.cpi(*old, 0, C_RESTART, eps)
+    r1, q, ost, _ = O.osp(old, g.csr(), r0, C_RESTART, eps)
+    assert st["net_inserts"] == 50 and st["net_deletes"] == 50
+    assert abs(st["iterations"] - ost["iterations"]) <= 1
+    assert l1(eng.query(), r1) <= 1e-10
+    r_cpi, _, _ = O.cpi(*g.csr(), 0, C_RESTART, 1e-15)
+    assert l1(eng.query(), r_cpi) <= 1e-10
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hub_lists_and_ospt_bounds(prec):
+    rng = np.random.default_rng(77)
+    n = 6000
+    src, dst = hub_graph(rng, n=n)
+    eps_init = 1e-13
+    eng, _ = engine(prec, n, src, dst, seed=2, eps_init=eps_init)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o, _, _ = O.cpi(*cur, 2, C_RESTART, eps_init)
+    es = W.EdgeSet(src, dst)
+    for b, eps in enumerate([1e-4, 1e-8, 1e-12, 1e-6]):
+        # touch the hub column, the heavy row and random rows
+        ins = np.array([(int(rng.integers(n)) << 32) | 1 for _ in range(30)]
+                       + [(2 << 32) | int(rng.integers(n)) for _ in range(30)], np.uint64)
+        ins = np.unique(ins[~es.contains(ins)])
+        ins = ins[(ins >> np.uint64(32)) != (ins & np.uint64(0xFFFFFFFF))]
+        dels = es.keys[rng.choice(es.keys.size, 200, replace=False)]
+        ops = W._pack(ins, dels, rng)
+        es.apply(ins, dels)
+        st = eng.apply_updates(ops, eps)
+        assert g.apply(ops) == -1
+        new = g.csr()
+        r_o, q, ost, _ = O.osp(cur, new, r_o, C_RESTART, eps, force_iters=st["iterations"])
+        cur = new
+        check_graph(eng, g)
+        assert l1(eng.query(), r_o) <= TOL[prec]
+        ql1 = float(np.abs(q).sum())
+        bound = 1 if ql1 <= eps else max(1, math.ceil(math.log(eps / ql1) / math.log(1 - C_RESTART)))
+        assert 1 <= st["iterations"] <= bound + 1
+    eng.close()
+
+
+def test_empty_and_noop_batches_leave_scores():
+    src, dst = W.er_graph(500, 4000, 21)
+    eng, _ = engine(N.OSP_PREC_FP64, 500, src, dst)
+    r0 = eng.query()
+    st = eng.apply_updates(np.zeros(0, W.UPDATE_DTYPE), 1e-12)
+    assert st["iterations"] == 1 and st["qoff_l1"] == 0.0
+    assert np.array_equal(eng.query(), r0)
+    ops = np.zeros(3, W.UPDATE_DTYPE)
+    ops[0] = (int(src[0]), int(dst[0]), 0)  # insert existing
+    have = set(zip(src.tolist(), dst.tolist()))
+    absent = [(u, v) for u in range(5) for v in range(5, 60) if (u, v) not in have][:2]
+    ops[1] = (absent[0][0], absent[0][1], 1)  # delete absent
+    ops[2] = (absent[1][0], absent[1][1], 1)
+    st = eng.apply_updates(ops, 1e-12)
+    assert st["net_inserts"] == 0 and st["net_deletes"] == 0 and st["changed_rows"] == 0
+    assert np.array_equal(eng.query(), r0)
+    eng.close()
+
+
+def test_dead_end_seed_and_new_nodes():
+    src = np.array([1, 2, 3], np.int32)
+    dst = np.array([0, 0, 1], np.int32)
+    eng, st = engine(N.OSP_PREC_FP64, 4, src, dst, seed=0, max_nodes=64)
+    r = eng.query()
+    assert r[0] == C_RESTART and np.all(r[1:] == 0)
+    ops = np.zeros(4, W.UPDATE_DTYPE)
+    ops[:] = [(0, 0, 2), (4, 0, 0), (0, 4, 0), (0, 2, 0)]
+    eng.apply_updates(ops, 1e-14)
+    g = O.Graph(4, src, dst)
+    assert g.apply(ops) == -1
+    check_graph(eng, g)
+    rp, col = g.csr()
+    r_cpi, _, _ = O.cpi(rp, col, 0, C_RESTART, 1e-15)
+    assert l1(eng.query(), r_cpi) < 1e-12
+    eng.close()
+
+
+def test_max_size_batch():
+    n = 20000
+    src, dst = W.er_graph(n, 120000, 33)
+    U = N.Engine.max_batch()
+    ops = W.edge_update_stream(src, dst, n, 1, U // 2, U - U // 2, seed=34)[0]
+    assert ops.size == U
+    eng, _ = engine(N.OSP_PREC_FP32_ACC64, n, src, dst, eps_init=1e-10)
+    st = eng.apply_updates(ops, 1e-6)
+    g = O.Graph(n, src, dst)
+    old = g.csr()
+    assert g.apply(ops) == -1
+    check_graph(eng, g)
+    r0, _, _ = O.cpi(*old, 0, C_RESTART, 1e-10)
+    r1, _, _, _ = O.osp(old, g.csr(), r0, C_RESTART, 1e-6, force_iters=st["iterations"])
+    assert l1(eng.query(), r1) <= 1e-5
+    with pytest.raises(N.OspError):
+        eng.apply_updates(np.zeros(U + 1, W.UPDATE_DTYPE), 1e-6)
+    eng.close()
+
+
+def test_pool_compaction_keeps_graph_exact():
+    rng = np.random.default_rng(5)
+    n = 3000
+    src, dst = hub_graph(rng, n=n, m=15000, hub_in=2500, hub_out=2500, mids=4)
+    eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, seed=7, eps_init=1e-12)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o, _, _ = O.cpi(*cur, 7, C_RESTART, 1e-12)
+    es = W.EdgeSet(src, dst)
+    for b in range(60):  # the hub lists are rewritten every batch: the pool fills and compacts
+        ins = np.array([(2 << 32) | int(x) for x in rng.integers(0, n, 20)]
+                       + [(int(x) << 32) | 1 for x in rng.integers(0, n, 20)], np.uint64)
+        ins = np.unique(ins[~es.contains(ins)])
+        ins = ins[(ins >> np.uint64(32)) != (ins & np.uint64(0xFFFFFFFF))]
+        dels = es.keys[rng.choice(es.keys.size, 40, replace=False)]
+        ops = W._pack(ins, dels, rng)
+        es.apply(ins, dels)
+        eng.apply_updates(ops, 1e-12)
+        assert g.apply(ops) == -1
+        new = g.csr()
+        r_o, _, _, _ = O.osp(cur, new, r_o, C_RESTART, 1e-12)
+        cur = new
+    check_graph(eng, g)
+    assert l1(eng.query(), r_o) <= 1e-10
+    eng.close()
+
+
+def test_rmat20_bench_configuration_sampled():
+    """The benchmark's workload at full size (R-MAT scale 20, 16.8M edges, seed of
+    highest out-degree, batches of 600 insertions + 400 deletions), a few batches,
+    both precisions against the oracle."""
+    gen, src, dst = W.rmat_graph(20, 1 << 24, seed=W.BASE_SEED + 2)
+    n = gen.n
+    seed = W.max_out_degree_seed(n, src)
+    stream = W.edge_update_stream(src, dst, n, 3, 600, 400, seed=W.BASE_SEED + 202,
+                                  sampler=gen.sample)
+    eps_init, eps = 1e-10, 1e-6
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    engs, chains = {}, {}
+    for prec in PRECS:
+        engs[prec], st0 = engine(prec, n, src, dst, seed=seed, eps_init=eps_init)
+        chains[prec], _, _ = O.cpi(*cur, seed, C_RESTART, eps_init, force_iters=st0["iterations"])
+        assert l1(engs[prec].query(), chains[prec]) <= TOL[prec]
+    for ops in stream:
+        assert g.apply(ops) == -1
+        new = g.csr()
+        for prec in PRECS:
+            st = engs[prec].apply_updates(ops, eps)
+            r_new, _, ost, _ = O.osp(cur, new, chains[prec], C_RESTART, eps,
+                                     force_iters=st["iterations"])
+            chains[prec] = r_new
+            assert l1(engs[prec].query(), r_new) <= TOL[prec]
+        cur = new
+    ptr, idx = engs[N.OSP_PREC_FP32_ACC64].export_graph(1)
+    cp, row = g.csc()
+    assert np.array_equal(ptr, cp) and np.array_equal(idx, row)
+    for e in engs.values():
+        e.close()
