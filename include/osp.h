@@ -159,7 +159,9 @@ osp_status osp_query(osp_ctx *ctx, int32_t seed_idx, int normalize, double *out)
 osp_status osp_query_device(osp_ctx *ctx, int32_t seed_idx, int normalize, double *out_device);
 
 /* The k highest-scoring nodes of seed seed_idx, ordered by score descending and
- * then id ascending (host outputs of k entries; fewer if n < k, count in *k_out). */
+ * then id ascending (host outputs of k entries; fewer if n < k, count in *k_out).
+ * 1 <= k <= 4096. normalize != 0 divides the returned scores by ||r||_1
+ * (Theorem 5); the ranking is the same either way. */
 osp_status osp_topk(osp_ctx *ctx, int32_t seed_idx, int32_t k, int normalize, int32_t *ids,
                     double *scores, int32_t *k_out);
 

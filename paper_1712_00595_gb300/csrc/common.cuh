@@ -87,6 +87,19 @@ struct Dev {
   Ctl* ctl;
 };
 
+// Radix-select state of a top-k query.
+struct TopkState {
+  unsigned long long prefix;  // selected leading bits of the order key
+  int bits;                   // how many leading bits are selected
+  int k_rem;                  // rank still to find inside the selected bin
+  int done;
+  int count;                  // survivors handed to the final sort
+  int above;                  // keys above the bin (all of them are in the top k)
+  int bin_count;              // keys inside the bin
+  int keep;                   // bin keys kept (all, or the k_rem smallest ids of one key value)
+  int pad;
+};
+
 struct PropParams {
   double eps;
   int max_iter;

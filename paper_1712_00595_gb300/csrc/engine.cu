@@ -54,6 +54,16 @@ struct osp_ctx {
   int* pool_spare = nullptr;  // compaction target
   unsigned long long spare_cap = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, propagation start, end
+  // top-k scratch
+  TopkState* tk_state = nullptr;
+  unsigned* tk_hist = nullptr;
+  int* tk_blk_a = nullptr;
+  int* tk_blk_b = nullptr;
+  unsigned long long* tk_keys = nullptr;
+  int* tk_ids = nullptr;
+  int* tk_out_ids = nullptr;
+  double* tk_out_sc = nullptr;
+  int* tk_out_k = nullptr;
 };
 
 namespace {
@@ -100,6 +110,12 @@ void free_all(osp_ctx* ctx) {
   ctx->scan_off = nullptr;
   ctx->scan_bsum = nullptr;
   ctx->pool_spare = nullptr;
+  ctx->tk_state = nullptr;
+  ctx->tk_hist = nullptr;
+  ctx->tk_blk_a = ctx->tk_blk_b = nullptr;
+  ctx->tk_keys = nullptr;
+  ctx->tk_ids = ctx->tk_out_ids = ctx->tk_out_k = nullptr;
+  ctx->tk_out_sc = nullptr;
 }
 
 // Sorted, de-duplicated adjacency lists of one direction from (key, val) pairs.
@@ -375,6 +391,9 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ingest, cudaFuncAttributeMaxDynamicSharedMemorySize, kIngestSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (kTopkMaxK + kTopkCand) * (int)(sizeof(unsigned long long) + sizeof(int)));
   if (e != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -514,6 +533,15 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(ctx->dtmp, nc, 0);
   AL(ctx->scan_off, nc, 0);
   AL(ctx->scan_bsum, nc / 4096 + 2, 0);
+  AL(ctx->tk_state, 1, 0);
+  AL(ctx->tk_hist, 4096, 0);
+  AL(ctx->tk_blk_a, nc / kTopkChunk + 2, 0);
+  AL(ctx->tk_blk_b, nc / kTopkChunk + 2, 0);
+  AL(ctx->tk_keys, kTopkMaxK + kTopkCand, 0);
+  AL(ctx->tk_ids, kTopkMaxK + kTopkCand, 0);
+  AL(ctx->tk_out_ids, kTopkMaxK, 0);
+  AL(ctx->tk_out_sc, kTopkMaxK, 0);
+  AL(ctx->tk_out_k, 1, 0);
 #undef AL
   CK(cudaMemcpyAsync(d.off_r, off_r.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d.len_r, len_r.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
@@ -648,8 +676,38 @@ osp_status osp_query(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out)
 
 osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, int32_t* ids,
                     double* scores, int32_t* k_out) {
-  (void)seed_idx; (void)k; (void)normalize; (void)ids; (void)scores; (void)k_out;
-  return fail(ctx, OSP_ENOTSUP, "top-k is not available in this build");
+  osp_status s = check_ready(ctx, true);
+  if (s != OSP_OK) return s;
+  if (seed_idx != 0 || k <= 0 || k > kTopkMaxK || !ids || !scores || !k_out)
+    return fail(ctx, OSP_EINVAL, "bad seed index, k outside [1, 4096] or null output");
+  const int n = (int)ctx->n;
+  const int g = ctx->num_sms * 4;
+  cudaStream_t st = ctx->stream;
+  k_topk_reset<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, k);
+  const int widths[6] = {12, 12, 12, 12, 12, 4};
+  for (int w : widths) {
+    k_topk_hist<<<g, 256, 0, st>>>(ctx->d.r, n, ctx->tk_state, ctx->tk_hist, w);
+    k_topk_select<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, w, kTopkCand);
+  }
+  const int nb = (n + kTopkChunk - 1) / kTopkChunk;
+  k_topk_count<<<nb, 1024, 0, st>>>(ctx->d.r, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b);
+  k_topk_scan<<<1, 32, 0, st>>>(ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b, nb, kTopkCand);
+  k_topk_emit<<<nb, 1024, 0, st>>>(ctx->d.r, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b,
+                                   ctx->tk_keys, ctx->tk_ids);
+  if (normalize) {
+    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), st));
+    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(ctx->d.r, n, ctx->dsum);
+  }
+  const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
+  k_topk_sort<<<1, 1024, smem, st>>>(ctx->d.r, ctx->tk_state, ctx->tk_keys, ctx->tk_ids,
+                                     kTopkMaxK + kTopkCand, k, normalize ? ctx->dsum : nullptr,
+                                     ctx->tk_out_ids, ctx->tk_out_sc, ctx->tk_out_k);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(k_out, ctx->tk_out_k, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ids, ctx->tk_out_ids, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(scores, ctx->tk_out_sc, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return OSP_OK;
 }
 
 osp_status osp_export_graph(osp_ctx* ctx, int direction, int64_t* ptr, int32_t* idx) {

@@ -23,6 +23,25 @@ __global__ void k_abs_sum(const double* __restrict__ r, int n, double* out);
 __global__ void k_scale_copy(const double* __restrict__ r, int n, const double* __restrict__ sum,
                              double* out);
 
+// Top-k (radix select + ordered compaction + one-CTA bitonic sort)
+__global__ void k_topk_reset(TopkState* st, unsigned* hist, int k);
+__global__ void k_topk_hist(const double* __restrict__ r, int n, const TopkState* __restrict__ st,
+                            unsigned* hist, int width);
+__global__ void k_topk_select(TopkState* st, unsigned* hist, int width, int cand_max);
+__global__ void k_topk_count(const double* __restrict__ r, int n, const TopkState* __restrict__ st,
+                             int* blk_above, int* blk_bin);
+__global__ void k_topk_scan(TopkState* st, int* blk_above, int* blk_bin, int nb, int cand_max);
+__global__ void k_topk_emit(const double* __restrict__ r, int n, const TopkState* __restrict__ st,
+                            const int* __restrict__ blk_above, const int* __restrict__ blk_bin,
+                            unsigned long long* keys, int* ids);
+__global__ void k_topk_sort(const double* __restrict__ r, const TopkState* __restrict__ st,
+                            const unsigned long long* keys, const int* ids, int cap, int k,
+                            const double* __restrict__ norm, int* out_ids, double* out_scores,
+                            int* out_k);
+constexpr int kTopkMaxK = 4096;
+constexpr int kTopkCand = 4096;
+constexpr int kTopkChunk = 4096;
+
 // Propagation (persistent, cooperative launch). T = double or float.
 template <typename T>
 __global__ void k_propagate(Dev d, PropParams pp);
