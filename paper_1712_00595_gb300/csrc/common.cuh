@@ -21,6 +21,7 @@ constexpr int kNoPos = 0x7F7F7F7F;       // del_pos of a node not deleted by the
 constexpr int kHubThreshold = 2048;      // in-lists longer than this are split into pieces
 constexpr int kHubPiece = 2048;          // edges per hub piece
 constexpr int kLight = 32;               // lists up to this length are walked by one lane
+constexpr int kPiece = 256;              // old entries per warp task in the list merge
 constexpr int kMaxHist = 4096;           // per-step ||x||_1 history entries
 constexpr int kMaxGrid = 4096;           // CTAs of the persistent kernel (partials array size)
 constexpr int kPropThreads = 256;
@@ -42,6 +43,8 @@ struct Ctl {
   int n_rec_r, n_rec_c;        // changed row / column records
   int n_del;                   // nodes deleted by the batch
   int n_hubs, n_pieces;
+  int n_mpieces;               // merge pieces of the current batch
+  int pad1;
   int epoch;                   // frontier mark of x(0); step i uses epoch + i
   int q_size[2];               // frontier queue lengths
   unsigned int bar_count, bar_gen;
@@ -79,6 +82,10 @@ struct Dev {
   int* rec_r_node; int* rec_r_is; int* rec_r_ic; int* rec_r_ds; int* rec_r_dc;  // [nc]
   int* rec_c_node; int* rec_c_is; int* rec_c_ic; int* rec_c_ds; int* rec_c_dc;  // [nc]
   int* del_nodes;  // [kMaxBatch]
+  // merge plan over the changed lists (out-lists first, then in-lists)
+  unsigned* rec_old_off; int* rec_old_len; int* rec_pstart;  // [2 nc + 1]
+  unsigned* rec_fbase; int* rec_dp;                          // [2 nc]
+  int* piece_rec; int* piece_cnt; int* piece_base;           // [2 nc + 2 pool cap / kPiece + 2]
   // hubs (long in-lists) for the pull step
   int* hubs; int* hub_pstart; double* hub_acc; int* hub_cnt;  // [pool cap / kHubThreshold + 2]
   // reductions and history

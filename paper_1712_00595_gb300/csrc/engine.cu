@@ -217,8 +217,8 @@ osp_status compact(osp_ctx* ctx, bool rows) {
 osp_status reserve_for_batch(osp_ctx* ctx, int64_t U) {
   if (ctx->n + U > ctx->nc)
     return fail(ctx, OSP_ENOMEM, "node capacity exhausted; create the context with a larger max_nodes");
-  // a batch writes at most 2 (m + U) entries per direction (scratch + final lists)
-  const unsigned long long need = 2ull * (unsigned long long)(ctx->m + U) + 64;
+  // a batch writes at most m + U entries per direction (the new lists)
+  const unsigned long long need = (unsigned long long)(ctx->m + U) + 64;
   if (ctx->cap_r - ctx->top_r < need) {
     osp_status s = compact(ctx, true);
     if (s != OSP_OK) return s;
@@ -328,8 +328,10 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
   k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
   k_ingest<<<1, 1024, (size_t)Np * 8, ctx->stream>>>(ctx->d, ops_dev, (int)U);
   k_expand<<<g, 256, 0, ctx->stream>>>(ctx->d);
-  k_merge_rows<<<g, 256, 0, ctx->stream>>>(ctx->d);
-  k_merge_cols<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  k_merge_pieces<<<1, 1024, 0, ctx->stream>>>(ctx->d);
+  k_merge_count<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  k_merge_plan<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  k_merge_write<<<g, 256, 0, ctx->stream>>>(ctx->d);
   CK(cudaGetLastError());
   s = run_propagation(ctx, eps);
   if (s != OSP_OK) return s;
@@ -518,6 +520,18 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(d.rec_c_ds, nc, 0);
   AL(d.rec_c_dc, nc, 0);
   AL(d.del_nodes, kMaxBatch, 0);
+  AL(d.rec_old_off, 2 * nc + 1, 0);
+  AL(d.rec_old_len, 2 * nc + 1, 0);
+  AL(d.rec_pstart, 2 * nc + 1, 0);
+  AL(d.rec_fbase, 2 * nc, 0);
+  AL(d.rec_dp, 2 * nc, 0);
+  {
+    // pieces: at most one per changed list plus one per kPiece old entries
+    const int64_t npc = 2 * nc + 2 * (int64_t)(cap / kPiece) + 2;
+    AL(d.piece_rec, npc, 0);
+    AL(d.piece_cnt, npc, 0);
+    AL(d.piece_base, npc, 0);
+  }
   // lists longer than kHubThreshold number at most (live edges) / kHubThreshold <= cap / kHubThreshold
   const int64_t nh = (int64_t)(cap / kHubThreshold) + 2;
   AL(d.hubs, nh, 0);

@@ -8,8 +8,10 @@ __global__ void k_reset_batch(Dev d);
 __global__ void k_cpi_begin(Dev d);
 __global__ void k_ingest(Dev d, const osp_update* __restrict__ ops, int U);
 __global__ void k_expand(Dev d);
-__global__ void k_merge_rows(Dev d);
-__global__ void k_merge_cols(Dev d);
+__global__ void k_merge_pieces(Dev d);
+__global__ void k_merge_count(Dev d);
+__global__ void k_merge_plan(Dev d);
+__global__ void k_merge_write(Dev d);
 __global__ void k_hubs(Dev d);
 __global__ void k_hub_prefix(Dev d);
 __global__ void k_set_scale(Dev d, int n, double c);

@@ -1,18 +1,22 @@
 // Delta-merge of the slotted graph store, fused with the offset vector.
 //
-// For every changed row u of the out-lists (one warp per row):
-//   * the old list A~[u] is read once; entries that survive go to scratch
-//     pool space, entries removed by the batch contribute
-//       q_offset[v] += (1-c) r_old[u] (0 - 1/d_u)
-//   * the surviving entries and the inserted ones are merged into fresh pool
-//     space (final positions by binary search, so every lane works alone);
-//     survivors contribute (1-c) r_old[u] (1/d'_u - 1/d_u) and insertions
-//     (1-c) r_old[u] / d'_u.
-// Together that is q_offset = (1-c) (B~^T - A~^T) r_old restricted to the rows
-// where B~ differs from A~ (Sec. 3.1, Algorithm 1 first step; Sec. 3.3 notes
-// that only the modified rows contribute). Every v that receives a
-// contribution enters the first frontier. The in-lists are merged the same
-// way without the offset.
+// Every changed list (out-list row u, or in-list column v) is cut into pieces
+// of kPiece old entries, and independent warps handle the pieces in three
+// passes, so a hub list costs no more latency than a short one:
+//   count  survivors of each piece (an entry goes if the batch deletes it or
+//          its other end is a node deleted by the batch); for out-lists the
+//          removed entries contribute q_offset[v] += (1-c) r_old[u] (0 - 1/d_u)
+//   plan   per list: exclusive scan of its pieces' survivor counts, new length
+//          d' = survivors + insertions, fresh pool space, new slot and (for
+//          out-lists) the new (1-c)/d'
+//   write  survivors go to rank + (insertions below them); each insertion goes
+//          to its index + (survivors below it); for out-lists survivors
+//          contribute (1-c) r_old[u] (1/d'_u - 1/d_u) and insertions
+//          (1-c) r_old[u] / d'_u.
+// The contributions add up to q_offset = (1-c) (B~^T - A~^T) r_old over the
+// rows where B~ differs from A~ (Sec. 3.1, Algorithm 1 first step; Sec. 3.3:
+// only the modified rows contribute). Every node that receives a contribution
+// joins the first frontier.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -25,119 +29,256 @@ __device__ __forceinline__ void offset_add(const Dev& d, bool want, int v, doubl
   warp_append(need, v, d.q0, &d.ctl->q_size[0]);
 }
 
-template <bool kRows>
-__device__ void merge_lists(const Dev& d) {
-  Ctl* ctl = d.ctl;
-  if (*(volatile int*)&ctl->status) return;
-  const int nrec = kRows ? ctl->n_rec_r : ctl->n_rec_c;
-  unsigned* off = kRows ? d.off_r : d.off_c;
-  int* len = kRows ? d.len_r : d.len_c;
-  int* pool = kRows ? d.pool_r : d.pool_c;
-  const int* ins = kRows ? d.ins_r : d.ins_c;
-  const int* del = kRows ? d.del_r : d.del_c;
-  const int* rnode = kRows ? d.rec_r_node : d.rec_c_node;
-  const int* ris = kRows ? d.rec_r_is : d.rec_c_is;
-  const int* ric = kRows ? d.rec_r_ic : d.rec_c_ic;
-  const int* rds = kRows ? d.rec_r_ds : d.rec_c_ds;
-  const int* rdc = kRows ? d.rec_r_dc : d.rec_c_dc;
-  unsigned long long* top = kRows ? &ctl->pool_top_r : &ctl->pool_top_c;
-  const unsigned long long cap = kRows ? ctl->pool_cap_r : ctl->pool_cap_c;
-  const double c = ctl->c;
-  const int epoch = ctl->epoch;
-  const bool any_dead = ctl->n_del > 0;
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  long long mdelta = 0;
+// One changed list, seen through the combined record index c (out-lists first).
+struct ListRec {
+  bool rows;
+  int node, is, ic, ds, dc;
+  const int* ins;
+  const int* del;
+  int* pool;
+};
 
-  for (int rec = gw; rec < nrec; rec += nw) {
-    const int u = rnode[rec];
-    const int is = ris[rec], ic = ric[rec], ds = rds[rec], dc = rdc[rec];
-    const unsigned o = off[u];
-    const int L = len[u];
-    const bool cleared = d.dead[u];
-    const double ru = kRows ? d.r[u] : 0.0;
-    const bool contrib = kRows && ru != 0.0;
-    const double wa = L ? 1.0 / (double)L : 0.0;
-
-    // survivors of the old list
-    const int* S;
-    int K;
-    if (dc == 0 && !any_dead && !cleared) {
-      S = pool + o;  // nothing removed: the old list is the survivor list
-      K = L;
-    } else {
-      unsigned long long sb = 0;
-      if (lane == 0 && L > 0) sb = atomicAdd(top, (unsigned long long)L);
-      sb = __shfl_sync(0xffffffffu, sb, 0);
-      if (sb + (unsigned long long)L > cap) {
-        if (lane == 0) atomicCAS(&ctl->status, 0, (int)OSP_ENOMEM);
-        return;
-      }
-      int* Sw = pool + sb;
-      K = 0;
-      for (int b = 0; b < L; b += 32) {
-        const int j = b + lane;
-        const bool in = j < L;
-        const int a = in ? pool[o + j] : 0;
-        const bool keep = in && !cleared && !d.dead[a] && !contains_i(del + ds, dc, a);
-        const unsigned bm = __ballot_sync(0xffffffffu, keep);
-        if (keep) Sw[K + __popc(bm & lanemask_lt())] = a;
-        K += __popc(bm);
-        if (contrib) offset_add(d, in && !keep, a, (1.0 - c) * ru * (0.0 - wa), epoch);
-      }
-      __syncwarp();
-      S = Sw;
-    }
-    const int dp = K + ic;
-    unsigned long long fb = 0;
-    if (lane == 0 && dp > 0) fb = atomicAdd(top, (unsigned long long)dp);
-    fb = __shfl_sync(0xffffffffu, fb, 0);
-    if (fb + (unsigned long long)dp > cap) {
-      if (lane == 0) atomicCAS(&ctl->status, 0, (int)OSP_ENOMEM);
-      return;
-    }
-    int* F = pool + fb;
-    const double wb = dp ? 1.0 / (double)dp : 0.0;
-    const bool shift = contrib && dp != L;
-    for (int b = 0; b < K; b += 32) {
-      const int k = b + lane;
-      const bool in = k < K;
-      const int a = in ? S[k] : 0;
-      if (in) F[k + lower_bound_i(ins + is, ic, a)] = a;
-      if (shift) offset_add(d, in, a, (1.0 - c) * ru * (wb - wa), epoch);
-    }
-    for (int b = 0; b < ic; b += 32) {
-      const int j = b + lane;
-      const bool in = j < ic;
-      const int e = in ? ins[is + j] : 0;
-      if (in) F[j + lower_bound_i(S, K, e)] = e;
-      if (contrib) offset_add(d, in, e, (1.0 - c) * ru * (wb - 0.0), epoch);
-    }
-    if (lane == 0) {
-      off[u] = (unsigned)fb;
-      len[u] = dp;
-      if (kRows) {
-        const double s = dp ? (1.0 - c) / (double)dp : 0.0;
-        d.scale_d[u] = s;
-        d.scale_f[u] = (float)s;
-        mdelta += dp - L;
-        d.rflag[u] = 0;
-      } else {
-        d.cflag[u] = 0;
-      }
-    }
+__device__ __forceinline__ ListRec list_rec(const Dev& d, int c, int n_rows) {
+  ListRec L;
+  L.rows = c < n_rows;
+  const int k = L.rows ? c : c - n_rows;
+  if (L.rows) {
+    L.node = d.rec_r_node[k];
+    L.is = d.rec_r_is[k];
+    L.ic = d.rec_r_ic[k];
+    L.ds = d.rec_r_ds[k];
+    L.dc = d.rec_r_dc[k];
+    L.ins = d.ins_r;
+    L.del = d.del_r;
+    L.pool = d.pool_r;
+  } else {
+    L.node = d.rec_c_node[k];
+    L.is = d.rec_c_is[k];
+    L.ic = d.rec_c_ic[k];
+    L.ds = d.rec_c_ds[k];
+    L.dc = d.rec_c_dc[k];
+    L.ins = d.ins_c;
+    L.del = d.del_c;
+    L.pool = d.pool_c;
   }
-  if (kRows) {
-    mdelta = warp_sum(mdelta);
-    if (lane == 0 && mdelta) atomicAdd((unsigned long long*)&ctl->m_delta, (unsigned long long)mdelta);
-  }
+  return L;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_merge_rows(Dev d) { merge_lists<true>(d); }
-__global__ void __launch_bounds__(256) k_merge_cols(Dev d) { merge_lists<false>(d); }
+// One CTA: list each changed list's pieces and remember its old slot.
+__global__ void __launch_bounds__(1024) k_merge_pieces(Dev d) {
+  __shared__ int s_w[32];
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int nr = ctl->n_rec_r;
+  const int R = nr + ctl->n_rec_c;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (R + 1023) / 1024;
+  const int lo = min(R, tid * per), hi = min(R, lo + per);
+  int mine = 0;
+  for (int c = lo; c < hi; ++c) {
+    const bool rows = c < nr;
+    const int node = rows ? d.rec_r_node[c] : d.rec_c_node[c - nr];
+    const unsigned o = rows ? d.off_r[node] : d.off_c[node];
+    const int L = rows ? d.len_r[node] : d.len_c[node];
+    d.rec_old_off[c] = o;
+    d.rec_old_len[c] = L;
+    mine += L > 0 ? (L + kPiece - 1) / kPiece : 1;
+  }
+  int x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = s_w[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    s_w[lane] = t;
+  }
+  __syncthreads();
+  int base = (w ? s_w[w - 1] : 0) + x - mine;
+  for (int c = lo; c < hi; ++c) {
+    const int L = d.rec_old_len[c];
+    const int np = L > 0 ? (L + kPiece - 1) / kPiece : 1;
+    d.rec_pstart[c] = base;
+    for (int q = 0; q < np; ++q) d.piece_rec[base + q] = c;
+    base += np;
+  }
+  if (tid == 0) {
+    ctl->n_mpieces = s_w[31];
+    d.rec_pstart[R] = s_w[31];
+  }
+}
+
+// Survivors per piece; removed out-list entries contribute to q_offset.
+__global__ void __launch_bounds__(256) k_merge_count(Dev d) {
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int np = ctl->n_mpieces, nr = ctl->n_rec_r;
+  const double c1 = 1.0 - ctl->c;
+  const int epoch = ctl->epoch;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = gw; p < np; p += nw) {
+    const int c = d.piece_rec[p];
+    const ListRec R = list_rec(d, c, nr);
+    const int q = p - d.rec_pstart[c];
+    const unsigned o = d.rec_old_off[c];
+    const int L = d.rec_old_len[c];
+    const bool cleared = d.dead[R.node];
+    const double ru = R.rows ? d.r[R.node] : 0.0;
+    const bool contrib = R.rows && ru != 0.0;
+    const double wa = L ? 1.0 / (double)L : 0.0;
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kPiece / 32; ++r) {
+      const int i = q * kPiece + r * 32 + lane;
+      const bool in = i < L;
+      const int a = in ? R.pool[o + i] : 0;
+      const bool keep = in && !cleared && !d.dead[a] && !contains_i(R.del + R.ds, R.dc, a);
+      cnt += __popc(__ballot_sync(0xffffffffu, keep));
+      if (contrib) offset_add(d, in && !keep, a, c1 * ru * (0.0 - wa), epoch);
+    }
+    if (lane == 0) d.piece_cnt[p] = cnt;
+  }
+}
+
+// Per list: piece bases, new length, fresh pool space, new slot.
+__global__ void __launch_bounds__(256) k_merge_plan(Dev d) {
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int nr = ctl->n_rec_r;
+  const int R = nr + ctl->n_rec_c;
+  const double c1 = 1.0 - ctl->c;
+  const unsigned long long cap_r = ctl->pool_cap_r, cap_c = ctl->pool_cap_c;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  long long mdelta = 0;
+  for (int c = gw; c < R; c += nw) {
+    const ListRec L = list_rec(d, c, nr);
+    const int p0 = d.rec_pstart[c], p1 = d.rec_pstart[c + 1];
+    int run = 0;
+    for (int b = p0; b < p1; b += 32) {  // exclusive scan of the piece counts
+      const int p = b + lane;
+      const int v = p < p1 ? d.piece_cnt[p] : 0;
+      int x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (p < p1) d.piece_base[p] = run + x - v;
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    const int dp = run + L.ic;
+    unsigned long long fb = 0;
+    if (lane == 0 && dp > 0)
+      fb = atomicAdd(L.rows ? &ctl->pool_top_r : &ctl->pool_top_c, (unsigned long long)dp);
+    fb = __shfl_sync(0xffffffffu, fb, 0);
+    if (fb + (unsigned long long)dp > (L.rows ? cap_r : cap_c)) {
+      if (lane == 0) atomicCAS(&ctl->status, 0, (int)OSP_ENOMEM);
+      return;
+    }
+    if (lane == 0) {
+      d.rec_fbase[c] = (unsigned)fb;
+      d.rec_dp[c] = dp;
+      if (L.rows) {
+        d.off_r[L.node] = (unsigned)fb;
+        d.len_r[L.node] = dp;
+        const double s = dp ? c1 / (double)dp : 0.0;
+        d.scale_d[L.node] = s;
+        d.scale_f[L.node] = (float)s;
+        mdelta += dp - d.rec_old_len[c];
+        d.rflag[L.node] = 0;
+      } else {
+        d.off_c[L.node] = (unsigned)fb;
+        d.len_c[L.node] = dp;
+        d.cflag[L.node] = 0;
+      }
+    }
+  }
+  mdelta = warp_sum(mdelta);
+  if (lane == 0 && mdelta) atomicAdd((unsigned long long*)&ctl->m_delta, (unsigned long long)mdelta);
+}
+
+// Survivors and insertions to their final positions; out-list contributions.
+__global__ void __launch_bounds__(256) k_merge_write(Dev d) {
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int np = ctl->n_mpieces, nr = ctl->n_rec_r;
+  const double c1 = 1.0 - ctl->c;
+  const int epoch = ctl->epoch;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = gw; p < np; p += nw) {
+    const int c = d.piece_rec[p];
+    const ListRec R = list_rec(d, c, nr);
+    const int q = p - d.rec_pstart[c];
+    const int npieces = d.rec_pstart[c + 1] - d.rec_pstart[c];
+    const unsigned o = d.rec_old_off[c];
+    const int L = d.rec_old_len[c];
+    const int dp = d.rec_dp[c];
+    int* F = R.pool + d.rec_fbase[c];
+    const int base = d.piece_base[p];
+    const int* I = R.ins + R.is;
+    const int ic = R.ic;
+    const bool cleared = d.dead[R.node];
+    const double ru = R.rows ? d.r[R.node] : 0.0;
+    const bool contrib = R.rows && ru != 0.0;
+    const double wa = L ? 1.0 / (double)L : 0.0;
+    const double wb = dp ? 1.0 / (double)dp : 0.0;
+    const bool shift = contrib && dp != L;
+    unsigned masks[kPiece / 32];
+    int run = 0;
+#pragma unroll
+    for (int r = 0; r < kPiece / 32; ++r) {
+      const int i = q * kPiece + r * 32 + lane;
+      const bool in = i < L;
+      const int a = in ? R.pool[o + i] : 0;
+      const bool keep = in && !cleared && !d.dead[a] && !contains_i(R.del + R.ds, R.dc, a);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      masks[r] = m;
+      if (keep) F[base + run + __popc(m & lanemask_lt()) + lower_bound_i(I, ic, a)] = a;
+      run += __popc(m);
+      if (shift) offset_add(d, keep, a, c1 * ru * (wb - wa), epoch);
+    }
+    // insertions that fall inside this piece of the old list
+    if (ic > 0) {
+      const int* A = R.pool + o;
+      const int a0 = q * kPiece;
+      const int a1 = min(L, a0 + kPiece);
+      const int jlo = q == 0 ? 0 : lower_bound_i(I, ic, A[a0 - 1] + 1);
+      // piece q takes the insertions whose place among the old entries is in [a0, a1)
+      // (the last piece also those above every old entry)
+      const int jhi = q == npieces - 1 ? ic : lower_bound_i(I, ic, A[a1 - 1]);
+      for (int jb = jlo; jb < jhi; jb += 32) {
+        const int j = jb + lane;
+        const bool in = j < jhi;
+        const int e = in ? I[j] : 0;
+        if (in) {
+          const int t = lower_bound_i(A + a0, a1 - a0, e);  // old entries of this piece below e
+          int kept = 0;
+#pragma unroll
+          for (int r = 0; r < kPiece / 32; ++r) {
+            const int lo_r = r * 32;
+            if (t >= lo_r + 32) kept += __popc(masks[r]);
+            else if (t > lo_r) kept += __popc(masks[r] & ((1u << (t - lo_r)) - 1u));
+          }
+          F[j + base + kept] = e;
+        }
+        if (contrib) offset_add(d, in, e, c1 * ru * (wb - 0.0), epoch);
+      }
+    }
+  }
+}
 
 // In-lists longer than kHubThreshold are summed in pieces by the pull step.
 __global__ void k_hubs(Dev d) {
