@@ -329,6 +329,8 @@ def run_ours(args, rank, world):
     ms, stats = run(eng, args.eps, 0)
     clk = clocks.stop()
     iters = warm_iters + [s["iterations"] for s in stats]
+    st_us = eng.get_step_times()
+    step_profile = {"x0": float(st_us[0]), "steps": [round(float(x), 1) for x in st_us[1:]]}
     r_mixed = eng.query()
     t_local = sum(ms) / 1e3
     t_max = dist_max(t_local, world)
@@ -354,8 +356,9 @@ def run_ours(args, rank, world):
         "push_iterations_per_step": float(np.mean([s["push_iterations"] for s in stats])),
         "qoff_l1_mean": float(np.mean([s["qoff_l1"] for s in stats])),
         "visited_edges_per_step": float(np.mean([s["visited_edges"] for s in stats])),
-        "gpu_launches": 8 * K,
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "clocks": clk,
+        "last_step_profile_us": step_profile,
     }
 
     if not args.no_extras:
@@ -394,7 +397,6 @@ def run_ours(args, rank, world):
         e.close()
         out["e2e"] = {"value": K / dt, "unit": "batches/s", "h2d_bytes_per_step": step_bytes,
                       "d2h_bytes_per_step": 8 * n, "result": "full score vector (osp_query)"}
-        out["gpu_launches"] = 8 * K
     else:
         out["e2e"] = None
 

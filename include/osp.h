@@ -85,7 +85,9 @@ typedef struct {
     double push_alpha;  /* sparse (push) steps while frontier out-edges <= m / alpha (0 = 14) */
     double push_beta;   /* ... and frontier size <= n / beta (0 = 24) */
     int32_t max_iter;   /* iteration cap; 0 = ceil(log_{1-c}(eps/2)) + 8 (Theorem 3) */
-    int32_t reserved;
+    int32_t node_order; /* internal node order: 0 = descending out-degree of the loaded graph
+                           (locality of the gathers), 1 = the caller's ids. Results are the
+                           same up to rounding order; every call uses the caller's ids. */
 } osp_options;
 
 /* Per-call statistics (the columns of Table 2 plus bookkeeping). */
@@ -105,6 +107,8 @@ typedef struct {
     int64_t push_reached;    /* sum over push steps of the nodes reached |F(i)| */
     float ms_update;         /* device time of ingest + graph merge + offset (CUDA events) */
     float ms_propagate;      /* device time of the propagation kernel (CUDA events) */
+    int32_t kernel_launches; /* kernels this call launched */
+    int32_t reserved;
 } osp_batch_stats;
 
 /* Fill *opt with defaults (FP32_ACC64, device 0, engine-owned stream). */
@@ -175,6 +179,11 @@ osp_status osp_get_size(osp_ctx *ctx, int64_t *n, int64_t *m);
 
 /* ||x(0)||_1 .. ||x(k)||_1 of the last init/apply call (host, up to cap entries). */
 osp_status osp_get_l1_history(osp_ctx *ctx, double *out, int32_t cap, int32_t *count);
+
+/* Device time in microseconds of the parts of the last init/apply propagation
+ * (device clock): entry 0 is the x(0) pass, entry i the step computing x(i).
+ * Up to cap entries; the count in *count. */
+osp_status osp_get_step_times(osp_ctx *ctx, double *us, int32_t cap, int32_t *count);
 
 /* Run the next propagations for exactly k steps regardless of eps (k > 0), or
  * go back to the eps rule (k = 0). Used to compare precisions step for step. */

@@ -36,15 +36,25 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), lib: str = None,
+          checked: bool = False) -> str:
+    """Compile the engine. checked=True adds -DOSP_CHECKED (device index checks
+    that report and skip a bad access) and writes libosp_gb300_checked.so."""
+    if checked:
+        extra = tuple(extra) + ("-DOSP_CHECKED",)
+        lib = lib or os.path.join(BUILD, "libosp_gb300_checked.so")
+        force = True
+    LIB_OUT = lib or LIB
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     objs = []
 
+    tag = "_checked" if checked else ""
+
     def one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, src.replace(".cu", tag + ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -55,13 +65,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = LIB_OUT + ".tmp%d" % os.getpid()
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True,
                        text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIB_OUT)
+    return LIB_OUT
 
 
 if __name__ == "__main__":

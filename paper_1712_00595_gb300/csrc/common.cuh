@@ -9,6 +9,7 @@
 // compaction pass when the pool runs low.
 #pragma once
 #include <cstdint>
+#include <cstdio>
 #include <cuda_runtime.h>
 
 #include "../../include/osp.h"
@@ -18,14 +19,15 @@ namespace osp {
 constexpr int kMaxBatch = 16384;        // ops per apply call (keys pack the op index in 14 bits)
 constexpr int kMaxNodes = (1 << 25) - 1; // ids fit in 25 bits
 constexpr int kNoPos = 0x7F7F7F7F;       // del_pos of a node not deleted by the batch (memset 0x7F)
-constexpr int kHubThreshold = 2048;      // in-lists longer than this are split into pieces
-constexpr int kHubPiece = 2048;          // edges per hub piece
 constexpr int kLight = 32;               // lists up to this length are walked by one lane
 constexpr int kPiece = 256;              // old entries per warp task in the list merge
 constexpr int kMaxHist = 4096;           // per-step ||x||_1 history entries
 constexpr int kMaxGrid = 4096;           // CTAs of the persistent kernel (partials array size)
 constexpr int kPropThreads = 256;
 constexpr int kPropWarps = kPropThreads / 32;
+constexpr int kHubThreshold = 1024;  // pull step: in-lists longer than this are summed in pieces
+constexpr int kHubPiece = 1024;      // pull step: edges per hub piece
+constexpr int kTaskItems = 1024;     // pull step: items (edges + nodes) per warp task
 
 enum StepMode : int { kPush = 0, kPull = 1 };
 
@@ -42,7 +44,8 @@ struct Ctl {
   long long net_ins, net_del;  // edge edits of the batch (node deletions not included)
   int n_rec_r, n_rec_c;        // changed row / column records
   int n_del;                   // nodes deleted by the batch
-  int n_hubs, n_pieces;
+  int n_hubs, n_pieces;        // pull step: long in-lists and their pieces
+  int n_tasks;                 // pull step: warp tasks
   int n_mpieces;               // merge pieces of the current batch
   int pad1;
   int epoch;                   // frontier mark of x(0); step i uses epoch + i
@@ -61,6 +64,11 @@ struct Ctl {
 // Every device pointer of one engine, passed to kernels by value.
 struct Dev {
   int nc;  // node capacity
+  // Nodes are stored in an internal order (by default: descending out-degree
+  // of the loaded graph, so the gather vector of the most-read sources is
+  // dense in memory); the C ABI speaks the caller's ids.
+  int* ext2int;  // [nc] caller id -> internal id (identity above the loaded ids)
+  int* int2ext;  // [nc] internal id -> caller id
   int grid_prop;
   // graph store
   unsigned* off_r; int* len_r; int* pool_r;
@@ -86,11 +94,17 @@ struct Dev {
   unsigned* rec_old_off; int* rec_old_len; int* rec_pstart;  // [2 nc + 1]
   unsigned* rec_fbase; int* rec_dp;                          // [2 nc]
   int* piece_rec; int* piece_cnt; int* piece_base;           // [2 nc + 2 pool cap / kPiece + 2]
-  // hubs (long in-lists) for the pull step
+  // pull-step plan: prefix of in-list lengths, warp tasks of about
+  // kTaskItems items (edges + nodes, lists never split), and the long in-lists
+  // summed in pieces
+  unsigned* pc;                       // [nc + 1]  pc[v] = sum of in-list lengths below v
+  int* task_first;                    // [(nc + pool cap) / kTaskItems + 2] first node of each warp task
   int* hubs; int* hub_pstart; double* hub_acc; int* hub_cnt;  // [pool cap / kHubThreshold + 2]
+  int* big_u; double* big_y;  // push step: rows longer than kHubThreshold [pool cap / kHubThreshold + 2]
   // reductions and history
   double* part_l1; long long* part_ef;  // [kMaxGrid]
   double* l1_hist;                      // [kMaxHist]
+  unsigned long long* step_ns;          // [kMaxHist + 1] device clock at kernel start and after each step
   Ctl* ctl;
 };
 
@@ -115,6 +129,21 @@ struct PropParams {
   double beta;
   int fp32;
 };
+
+// ---------------------------------------------------------------------------
+// Checked builds (-DOSP_CHECKED): index checks that report the first bad
+// access, set an error status and skip the access instead of performing it.
+// ---------------------------------------------------------------------------
+#ifdef OSP_CHECKED
+#define OSP_GUARD(ctl, cond, what, a, b, c)                                             \
+  ((cond) ? true                                                                        \
+          : (printf("osp check failed: %s (%lld %lld %lld) block %d thread %d\n", what, \
+                    (long long)(a), (long long)(b), (long long)(c), blockIdx.x,         \
+                    threadIdx.x),                                                       \
+             atomicCAS(&(ctl)->status, 0, (int)OSP_ECUDA), false))
+#else
+#define OSP_GUARD(ctl, cond, what, a, b, c) true
+#endif
 
 // ---------------------------------------------------------------------------
 // small device helpers

@@ -54,6 +54,8 @@ struct osp_ctx {
   int* pool_spare = nullptr;  // compaction target
   unsigned long long spare_cap = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, propagation start, end
+  int launches = 0;  // kernels launched by the current call
+  std::vector<int32_t> e2i, i2e;  // caller id <-> internal id (identity above the loaded ids)
   // top-k scratch
   TopkState* tk_state = nullptr;
   unsigned* tk_hist = nullptr;
@@ -154,6 +156,36 @@ void build_lists(int64_t n, const std::vector<int32_t>& key, const std::vector<i
     std::memcpy(pool.data() + off[u], tmp.data() + start[u], sizeof(int) * len[u]);
 }
 
+// The same adjacency under the internal ids: list of internal node i is the
+// list of caller node i2e[i], each entry mapped by e2i and re-sorted.
+void relabel_lists(int64_t n, const std::vector<int32_t>& e2i, const std::vector<int32_t>& i2e,
+                   const std::vector<unsigned>& off, const std::vector<int>& len,
+                   const std::vector<int>& pool, std::vector<unsigned>& off2, std::vector<int>& len2,
+                   std::vector<int>& pool2) {
+  off2.assign(n, 0);
+  len2.assign(n, 0);
+  int64_t tot = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    off2[i] = (unsigned)tot;
+    len2[i] = len[i2e[i]];
+    tot += len2[i];
+  }
+  pool2.resize(tot);
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) {
+    th.emplace_back([&, t]() {
+      for (int64_t i = t; i < n; i += nt) {
+        const int u = i2e[i];
+        int* dst = pool2.data() + off2[i];
+        for (int k = 0; k < len[u]; ++k) dst[k] = e2i[pool[off[u] + k]];
+        std::sort(dst, dst + len[u]);
+      }
+    });
+  }
+  for (auto& x : th) x.join();
+}
+
 osp_status read_ctl(osp_ctx* ctx, Ctl* out) {
   CK(cudaMemcpyAsync(ctx->pinned, ctx->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -187,10 +219,14 @@ osp_status compact(osp_ctx* ctx, bool rows) {
   const int nb = (n + 4095) / 4096;
   if (n > 0) {
     k_scan_local<<<nb, 1024, 0, ctx->stream>>>(len, ctx->scan_off, ctx->scan_bsum, n);
+    ++ctx->launches;
     k_scan_top<<<1, 1024, 0, ctx->stream>>>(ctx->scan_bsum, nb);
+    ++ctx->launches;
     k_scan_add<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->scan_off, ctx->scan_bsum, n);
+    ++ctx->launches;
     k_compact_copy<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(off, len, pool, ctx->scan_off,
                                                                ctx->pool_spare, n);
+    ++ctx->launches;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(off, ctx->scan_off, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice,
                        ctx->stream));
@@ -250,6 +286,7 @@ void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_befor
   cudaMemcpy(&hist[1], ctx->d.l1_hist + k, sizeof(double), cudaMemcpyDeviceToHost);
   st->qoff_l1 = hist[0];
   st->last_x_l1 = hist[1];
+  st->kernel_launches = ctx->launches;
   st->push_frontier = h.push_f;
   st->push_reached = h.push_r;
   float a = 0.f, b = 0.f;
@@ -284,7 +321,31 @@ osp_status finish_call(osp_ctx* ctx, int64_t m_before, osp_batch_stats* st) {
   return OSP_OK;
 }
 
-osp_status run_propagation(osp_ctx* ctx, double eps) {
+// Pull-step plan for the graph as it is after the merge: in-list length prefix
+// over the first n_bound + 1 ids (ids at or above n have empty lists) and the
+// merge-path tile starts.
+osp_status plan_pull(osp_ctx* ctx, int64_t n_bound, int64_t m_bound) {
+  (void)m_bound;
+  const int ns = (int)std::min<int64_t>(n_bound + 1, ctx->nc);
+  const int nb = (ns + 4095) / 4096;
+  cudaStream_t st = ctx->stream;
+  k_merge_finish<<<1, 1, 0, st>>>(ctx->d);
+  ++ctx->launches;
+  k_scan_local<<<nb, 1024, 0, st>>>(ctx->d.len_c, ctx->d.pc, ctx->scan_bsum, ns);
+  ++ctx->launches;
+  k_scan_top<<<1, 1024, 0, st>>>(ctx->scan_bsum, nb);
+  ++ctx->launches;
+  k_scan_add<<<(ns + 255) / 256, 256, 0, st>>>(ctx->d.pc, ctx->scan_bsum, ns);
+  ++ctx->launches;
+  k_pull_plan<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d);
+  ++ctx->launches;
+  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d);
+  ++ctx->launches;
+  CK(cudaGetLastError());
+  return OSP_OK;
+}
+
+osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_bound) {
   PropParams pp;
   pp.eps = eps;
   pp.max_iter = default_max_iter(ctx, eps);
@@ -293,12 +354,11 @@ osp_status run_propagation(osp_ctx* ctx, double eps) {
   pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : 14.0;
   pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : 24.0;
   pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
-  const int g = ctx->num_sms * 4;
-  k_hubs<<<g, 256, 0, ctx->stream>>>(ctx->d);
-  k_hub_prefix<<<1, 1024, 0, ctx->stream>>>(ctx->d);
-  CK(cudaGetLastError());
+  osp_status s = plan_pull(ctx, n_bound, m_bound);
+  if (s != OSP_OK) return s;
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
   CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
+  ++ctx->launches;
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
   return OSP_OK;
 }
@@ -317,6 +377,7 @@ osp_status check_ready(osp_ctx* ctx, bool need_scores) {
 osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, double eps,
                         osp_batch_stats* st) {
   if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  ctx->launches = 0;
   osp_status s = reserve_for_batch(ctx, U);
   if (s != OSP_OK) return s;
   const int64_t m_before = ctx->m;
@@ -326,14 +387,21 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
   while (Np < N) Np <<= 1;
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
   k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   k_ingest<<<1, 1024, (size_t)Np * 8, ctx->stream>>>(ctx->d, ops_dev, (int)U);
+  ++ctx->launches;
   k_expand<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   k_merge_pieces<<<1, 1024, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   k_merge_count<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   k_merge_plan<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   k_merge_write<<<g, 256, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   CK(cudaGetLastError());
-  s = run_propagation(ctx, eps);
+  s = run_propagation(ctx, eps, std::min<int64_t>(ctx->n + U, ctx->nc - 1), ctx->m + U);
   if (s != OSP_OK) return s;
   return finish_call(ctx, m_before, st);
 }
@@ -455,6 +523,25 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   build_lists(n, a, b, off_r, len_r, pool_r);
   build_lists(n, b, a, off_c, len_c, pool_c);
   const int64_t mm = (int64_t)pool_r.size();
+  // internal order: descending out-degree (ties by id), or the caller's ids
+  std::vector<int32_t> i2e(n), e2i(n);
+  for (int64_t i = 0; i < n; ++i) i2e[i] = (int32_t)i;
+  if (ctx->opt.node_order == 0)
+    std::stable_sort(i2e.begin(), i2e.end(),
+                     [&](int32_t x, int32_t y) { return len_r[x] > len_r[y]; });
+  for (int64_t i = 0; i < n; ++i) e2i[i2e[i]] = (int32_t)i;
+  {
+    std::vector<unsigned> o2;
+    std::vector<int> l2, p2;
+    relabel_lists(n, e2i, i2e, off_r, len_r, pool_r, o2, l2, p2);
+    off_r.swap(o2);
+    len_r.swap(l2);
+    pool_r.swap(p2);
+    relabel_lists(n, e2i, i2e, off_c, len_c, pool_c, o2, l2, p2);
+    off_c.swap(o2);
+    len_c.swap(l2);
+    pool_c.swap(p2);
+  }
 
   int64_t nc = ctx->opt.max_nodes > 0 ? ctx->opt.max_nodes : n + n / 4 + 4096;
   nc = std::max<int64_t>(nc, n + kMaxBatch);
@@ -465,6 +552,11 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   ctx->nc = nc;
   ctx->n = n;
   ctx->m = mm;
+  ctx->e2i = e2i;
+  ctx->i2e = i2e;
+  ctx->e2i.resize(nc);
+  ctx->i2e.resize(nc);
+  for (int64_t x = n; x < nc; ++x) ctx->e2i[x] = ctx->i2e[x] = (int32_t)x;
   ctx->cap_r = ctx->cap_c = ctx->spare_cap = cap;
   ctx->top_r = ctx->top_c = (unsigned long long)mm;
 
@@ -479,6 +571,8 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
       return s;                                   \
     }                                             \
   } while (0)
+  AL(d.ext2int, nc, 0);
+  AL(d.int2ext, nc, 0);
   AL(d.off_r, nc, 0);
   AL(d.len_r, nc, 0);
   AL(d.off_c, nc, 0);
@@ -532,15 +626,22 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
     AL(d.piece_cnt, npc, 0);
     AL(d.piece_base, npc, 0);
   }
-  // lists longer than kHubThreshold number at most (live edges) / kHubThreshold <= cap / kHubThreshold
-  const int64_t nh = (int64_t)(cap / kHubThreshold) + 2;
-  AL(d.hubs, nh, 0);
-  AL(d.hub_pstart, nh + 1, 0);
-  AL(d.hub_acc, nh, 0);
-  AL(d.hub_cnt, nh, 0);
+  AL(d.pc, nc + 1, 0);
+  AL(d.task_first, (int64_t)(nc + (int64_t)cap) / kTaskItems + 2, 0);
+  {
+    // lists longer than kHubThreshold number at most (live edges) / kHubThreshold <= cap / kHubThreshold
+    const int64_t nh = (int64_t)(cap / kHubThreshold) + 2;
+    AL(d.hubs, nh, 0);
+    AL(d.hub_pstart, nh + 1, 0);
+    AL(d.hub_acc, nh, 0);
+    AL(d.hub_cnt, nh, 0);
+    AL(d.big_u, nh, 0);
+    AL(d.big_y, nh, 0);
+  }
   AL(d.part_l1, kMaxGrid, 0);
   AL(d.part_ef, kMaxGrid, 0);
   AL(d.l1_hist, kMaxHist, 0);
+  AL(d.step_ns, kMaxHist + 1, 0);
   AL(d.ctl, 1, 0);
   AL(ctx->ops_stage, kMaxBatch, 0);
   AL(ctx->dsum, 1, 0);
@@ -557,6 +658,8 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(ctx->tk_out_sc, kTopkMaxK, 0);
   AL(ctx->tk_out_k, 1, 0);
 #undef AL
+  CK(cudaMemcpyAsync(d.ext2int, ctx->e2i.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d.int2ext, ctx->i2e.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d.off_r, off_r.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d.len_r, len_r.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d.off_c, off_c.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, ctx->stream));
@@ -592,19 +695,21 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
   if (!seeds || !(c > 0.0 && c < 1.0)) return fail(ctx, OSP_EINVAL, "bad seed list or c");
   if (seeds[0] < 0 || seeds[0] >= ctx->n) return fail(ctx, OSP_EINVAL, "seed id out of range");
   CK(cudaSetDevice(ctx->device));
+  const int32_t s_int = ctx->e2i[seeds[0]];
   unsigned char dead = 0;
-  CK(cudaMemcpy(&dead, ctx->d.dead + seeds[0], 1, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&dead, ctx->d.dead + s_int, 1, cudaMemcpyDeviceToHost));
   if (dead) return fail(ctx, OSP_EINVAL, "seed is a deleted node");
   Ctl h;
   osp_status s = read_ctl(ctx, &h);
   if (s != OSP_OK) return s;
-  h.seed = seeds[0];
+  h.seed = s_int;
   h.c = c;
   s = write_ctl(ctx, h);
   if (s != OSP_OK) return s;
   ctx->seed = seeds[0];
   ctx->c = c;
   k_set_scale<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->d, (int)ctx->n, c);
+  ++ctx->launches;
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -618,12 +723,15 @@ osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
   osp_status s = check_ready(ctx, false);
   if (s != OSP_OK) return s;
   if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  ctx->launches = 0;
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
   CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
   k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   k_cpi_begin<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  ++ctx->launches;
   CK(cudaGetLastError());
-  s = run_propagation(ctx, eps);
+  s = run_propagation(ctx, eps, ctx->n, ctx->m);
   if (s != OSP_OK) return s;
   s = finish_call(ctx, ctx->m, stats);
   if (s == OSP_OK || s == OSP_ENOCONV) ctx->scored = true;
@@ -653,19 +761,26 @@ osp_status osp_apply_updates(osp_ctx* ctx, const osp_update* ops, int64_t U, dou
   return apply_common(ctx, ctx->ops_stage, U, eps, stats);
 }
 
+// Scores in caller order into dst (device), optionally divided by ||r||_1.
+osp_status scores_in_caller_order(osp_ctx* ctx, int normalize, double* dst) {
+  const int n = (int)ctx->n;
+  cudaStream_t st = ctx->stream;
+  k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dst);
+  if (normalize) {
+    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), st));
+    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(dst, n, ctx->dsum);
+    k_scale_copy<<<ctx->num_sms * 2, 256, 0, st>>>(dst, n, ctx->dsum, dst);
+  }
+  CK(cudaGetLastError());
+  return OSP_OK;
+}
+
 osp_status osp_query_device(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out_device) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
   if (seed_idx != 0 || !out_device) return fail(ctx, OSP_EINVAL, "bad seed index or output");
-  const int n = (int)ctx->n;
-  if (normalize) {
-    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), ctx->stream));
-    k_abs_sum<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum);
-    k_scale_copy<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum, out_device);
-    CK(cudaGetLastError());
-  } else {
-    CK(cudaMemcpyAsync(out_device, ctx->d.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-  }
+  s = scores_in_caller_order(ctx, normalize, out_device);
+  if (s != OSP_OK) return s;
   CK(cudaStreamSynchronize(ctx->stream));
   return OSP_OK;
 }
@@ -674,16 +789,9 @@ osp_status osp_query(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out)
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
   if (seed_idx != 0 || !out) return fail(ctx, OSP_EINVAL, "bad seed index or output");
-  const int n = (int)ctx->n;
-  const double* src = ctx->d.r;
-  if (normalize) {
-    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), ctx->stream));
-    k_abs_sum<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum);
-    k_scale_copy<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(ctx->d.r, n, ctx->dsum, ctx->dtmp);
-    CK(cudaGetLastError());
-    src = ctx->dtmp;
-  }
-  CK(cudaMemcpyAsync(out, src, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  s = scores_in_caller_order(ctx, normalize, ctx->dtmp);
+  if (s != OSP_OK) return s;
+  CK(cudaMemcpyAsync(out, ctx->dtmp, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return OSP_OK;
 }
@@ -697,25 +805,37 @@ osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, in
   const int n = (int)ctx->n;
   const int g = ctx->num_sms * 4;
   cudaStream_t st = ctx->stream;
+  // rank the scores in caller order, so that ties go to the smaller caller id
+  s = scores_in_caller_order(ctx, 0, ctx->dtmp);
+  if (s != OSP_OK) return s;
+  const double* rs = ctx->dtmp;
   k_topk_reset<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, k);
+  ++ctx->launches;
   const int widths[6] = {12, 12, 12, 12, 12, 4};
   for (int w : widths) {
-    k_topk_hist<<<g, 256, 0, st>>>(ctx->d.r, n, ctx->tk_state, ctx->tk_hist, w);
+    k_topk_hist<<<g, 256, 0, st>>>(rs, n, ctx->tk_state, ctx->tk_hist, w);
+    ++ctx->launches;
     k_topk_select<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, w, kTopkCand);
+    ++ctx->launches;
   }
   const int nb = (n + kTopkChunk - 1) / kTopkChunk;
-  k_topk_count<<<nb, 1024, 0, st>>>(ctx->d.r, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b);
+  k_topk_count<<<nb, 1024, 0, st>>>(rs, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b);
+  ++ctx->launches;
   k_topk_scan<<<1, 32, 0, st>>>(ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b, nb, kTopkCand);
-  k_topk_emit<<<nb, 1024, 0, st>>>(ctx->d.r, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b,
+  ++ctx->launches;
+  k_topk_emit<<<nb, 1024, 0, st>>>(rs, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b,
                                    ctx->tk_keys, ctx->tk_ids);
+  ++ctx->launches;
   if (normalize) {
     CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), st));
-    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(ctx->d.r, n, ctx->dsum);
+    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(rs, n, ctx->dsum);
+    ++ctx->launches;
   }
   const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
-  k_topk_sort<<<1, 1024, smem, st>>>(ctx->d.r, ctx->tk_state, ctx->tk_keys, ctx->tk_ids,
+  k_topk_sort<<<1, 1024, smem, st>>>(rs, ctx->tk_state, ctx->tk_keys, ctx->tk_ids,
                                      kTopkMaxK + kTopkCand, k, normalize ? ctx->dsum : nullptr,
                                      ctx->tk_out_ids, ctx->tk_out_sc, ctx->tk_out_k);
+  ++ctx->launches;
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(k_out, ctx->tk_out_k, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ids, ctx->tk_out_ids, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
@@ -741,10 +861,12 @@ osp_status osp_export_graph(osp_ctx* ctx, int direction, int64_t* ptr, int32_t* 
   CK(cudaMemcpy(len.data(), rows ? ctx->d.len_r : ctx->d.len_c, sizeof(int) * n, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(pool.data(), rows ? ctx->d.pool_r : ctx->d.pool_c, sizeof(int) * top, cudaMemcpyDeviceToHost));
   int64_t e = 0;
-  for (int64_t u = 0; u < n; ++u) {
+  for (int64_t u = 0; u < n; ++u) {  // caller node u is internal node e2i[u]
     ptr[u] = e;
-    if (len[u] > 0) std::memcpy(idx + e, pool.data() + off[u], sizeof(int) * len[u]);
-    e += len[u];
+    const int32_t i = ctx->e2i[u];
+    for (int k = 0; k < len[i]; ++k) idx[e + k] = ctx->i2e[pool[off[i] + k]];
+    std::sort(idx + e, idx + e + len[i]);
+    e += len[i];
   }
   ptr[n] = e;
   return OSP_OK;
@@ -762,6 +884,17 @@ osp_status osp_get_l1_history(osp_ctx* ctx, double* out, int32_t cap, int32_t* c
   if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
   const int k = std::min(std::min(ctx->last_iters + 1, kMaxHist), (int)cap);
   CK(cudaMemcpy(out, ctx->d.l1_hist, sizeof(double) * k, cudaMemcpyDeviceToHost));
+  *count = k;
+  return OSP_OK;
+}
+
+osp_status osp_get_step_times(osp_ctx* ctx, double* us, int32_t cap, int32_t* count) {
+  if (!ctx || !us || !count || cap < 0) return OSP_EINVAL;
+  if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
+  const int k = std::min(std::min(ctx->last_iters + 1, kMaxHist), (int)cap);
+  std::vector<unsigned long long> t(k + 1);
+  CK(cudaMemcpy(t.data(), ctx->d.step_ns, sizeof(unsigned long long) * (k + 1), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < k; ++i) us[i] = (double)(t[i + 1] - t[i]) * 1e-3;
   *count = k;
   return OSP_OK;
 }

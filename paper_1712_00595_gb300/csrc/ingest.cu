@@ -61,6 +61,16 @@ __device__ void bitonic_sort(unsigned long long* a, int N) {
   }
 }
 
+// An op with its node ids mapped to the engine's internal order. The map is a
+// permutation of the loaded ids and the identity above them, so an id is in
+// range before the mapping exactly when it is in range after it.
+__device__ __forceinline__ osp_update load_op(const osp_update* ops, int p, const Dev& d) {
+  osp_update o = ops[p];
+  if (o.u >= 0 && o.u < d.nc) o.u = d.ext2int[o.u];
+  if (o.v >= 0 && o.v < d.nc) o.v = d.ext2int[o.v];
+  return o;
+}
+
 __device__ __forceinline__ int next_pow2(int x) {
   int p = 2;
   while (p < x) p <<= 1;
@@ -153,8 +163,6 @@ __global__ void k_reset_batch(Dev d) {
   c->n_rec_r = 0;
   c->n_rec_c = 0;
   c->n_del = 0;
-  c->n_hubs = 0;
-  c->n_pieces = 0;
   c->q_size[0] = 0;
   c->q_size[1] = 0;
   for (int i = 0; i < 4; ++i) c->ctr[i] = 0;
@@ -205,7 +213,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   const int add_base = block_exscan(adds, &tot_adds);
   int run = add_base;
   for (int p = lo; p < hi; ++p) {
-    osp_update o = ops[p];
+    osp_update o = load_op(ops, p, d);
     if (o.op == OSP_OP_ADD_NODE) {
       ++run;
     } else if (o.op == OSP_OP_DELETE_NODE) {
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   __syncthreads();
   run = add_base;
   for (int p = lo; p < hi; ++p) {
-    osp_update o = ops[p];
+    osp_update o = load_op(ops, p, d);
     const int na = n_old + run;
     bool ok;
     if (o.op == OSP_OP_INSERT_EDGE || o.op == OSP_OP_DELETE_EDGE) {
@@ -237,8 +245,10 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   __syncthreads();
   if (s_bad != kNoPos) {
     for (int p = lo; p < hi; ++p)
-      if (ops[p].op == OSP_OP_DELETE_NODE && ops[p].u >= 0 && ops[p].u < d.nc)
-        d.del_pos[ops[p].u] = kNoPos;
+      if (ops[p].op == OSP_OP_DELETE_NODE) {
+        const osp_update o = load_op(ops, p, d);
+        if (o.u >= 0 && o.u < d.nc) d.del_pos[o.u] = kNoPos;
+      }
     if (tid == 0) {
       ctl->status = OSP_EINVAL;
       ctl->bad_op = s_bad;
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   // ---- canonical order: sort edge ops by (u, v, position) ----
   const int N = next_pow2(U);
   for (int p = lo; p < hi; ++p) {
-    osp_update o = ops[p];
+    osp_update o = load_op(ops, p, d);
     unsigned long long key = kNoKey;
     if ((o.op == OSP_OP_INSERT_EDGE || o.op == OSP_OP_DELETE_EDGE) && d.del_pos[o.u] == kNoPos &&
         d.del_pos[o.v] == kNoPos)
@@ -332,10 +342,10 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
 
   // ---- node deletions and additions ----
   for (int p = lo; p < hi; ++p)
-    if (ops[p].op == OSP_OP_DELETE_NODE) d.del_nodes[atomicAdd(&s_ndel, 1)] = ops[p].u;
+    if (ops[p].op == OSP_OP_DELETE_NODE) d.del_nodes[atomicAdd(&s_ndel, 1)] = load_op(ops, p, d).u;
   __syncthreads();
   for (int p = lo; p < hi; ++p)
-    if (ops[p].op == OSP_OP_DELETE_NODE) d.del_pos[ops[p].u] = kNoPos;
+    if (ops[p].op == OSP_OP_DELETE_NODE) d.del_pos[load_op(ops, p, d).u] = kNoPos;
   if (tid == 0) {
     ctl->n_del = s_ndel;
     ctl->n = n_old + tot_adds;

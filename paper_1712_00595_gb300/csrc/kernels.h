@@ -12,7 +12,8 @@ __global__ void k_merge_pieces(Dev d);
 __global__ void k_merge_count(Dev d);
 __global__ void k_merge_plan(Dev d);
 __global__ void k_merge_write(Dev d);
-__global__ void k_hubs(Dev d);
+__global__ void k_merge_finish(Dev d);
+__global__ void k_pull_plan(Dev d);
 __global__ void k_hub_prefix(Dev d);
 __global__ void k_set_scale(Dev d, int n, double c);
 __global__ void k_scan_local(const int* __restrict__ len, unsigned* out, unsigned* bsum, int n);
@@ -22,8 +23,9 @@ __global__ void k_compact_copy(const unsigned* __restrict__ off_old, const int* 
                                const int* __restrict__ pool_old, const unsigned* __restrict__ off_new,
                                int* pool_new, int n);
 __global__ void k_abs_sum(const double* __restrict__ r, int n, double* out);
-__global__ void k_scale_copy(const double* __restrict__ r, int n, const double* __restrict__ sum,
+__global__ void k_gather_ext(const double* __restrict__ r, const int* __restrict__ ext2int, int n,
                              double* out);
+__global__ void k_scale_copy(const double* r, int n, const double* __restrict__ sum, double* out);
 
 // Top-k (radix select + ordered compaction + one-CTA bitonic sort)
 __global__ void k_topk_reset(TopkState* st, unsigned* hist, int k);

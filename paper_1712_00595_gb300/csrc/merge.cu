@@ -24,6 +24,7 @@ namespace osp {
 namespace {
 
 __device__ __forceinline__ void offset_add(const Dev& d, bool want, int v, double val, int epoch) {
+  if (want && !OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "offset target", v, 0, 0)) want = false;
   if (want) atomicAdd(&d.xacc[v], val);
   bool need = want && (d.mark[v] != epoch) && (atomicExch(&d.mark[v], epoch) != epoch);
   warp_append(need, v, d.q0, &d.ctl->q_size[0]);
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
     for (int r = 0; r < kPiece / 32; ++r) {
       const int i = q * kPiece + r * 32 + lane;
       const bool in = i < L;
-      const int a = in ? R.pool[o + i] : 0;
+      int a = in ? R.pool[o + i] : 0;
+      if (in && !OSP_GUARD(d.ctl, a >= 0 && a < d.nc, "merge count entry", c, i, a)) a = 0;
       const bool keep = in && !cleared && !d.dead[a] && !contains_i(R.del + R.ds, R.dc, a);
       cnt += __popc(__ballot_sync(0xffffffffu, keep));
       if (contrib) offset_add(d, in && !keep, a, c1 * ru * (0.0 - wa), epoch);
@@ -242,11 +244,15 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
     for (int r = 0; r < kPiece / 32; ++r) {
       const int i = q * kPiece + r * 32 + lane;
       const bool in = i < L;
-      const int a = in ? R.pool[o + i] : 0;
+      int a = in ? R.pool[o + i] : 0;
+      if (in && !OSP_GUARD(d.ctl, a >= 0 && a < d.nc, "merge write entry", c, i, a)) a = 0;
       const bool keep = in && !cleared && !d.dead[a] && !contains_i(R.del + R.ds, R.dc, a);
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       masks[r] = m;
-      if (keep) F[base + run + __popc(m & lanemask_lt()) + lower_bound_i(I, ic, a)] = a;
+      if (keep) {
+        const int pos = base + run + __popc(m & lanemask_lt()) + lower_bound_i(I, ic, a);
+        if (OSP_GUARD(d.ctl, pos >= 0 && pos < dp, "merge write position", c, pos, dp)) F[pos] = a;
+      }
       run += __popc(m);
       if (shift) offset_add(d, keep, a, c1 * ru * (wb - wa), epoch);
     }
@@ -272,7 +278,8 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
             if (t >= lo_r + 32) kept += __popc(masks[r]);
             else if (t > lo_r) kept += __popc(masks[r] & ((1u << (t - lo_r)) - 1u));
           }
-          F[j + base + kept] = e;
+          if (OSP_GUARD(d.ctl, j + base + kept < dp, "merge insert position", c, j + base + kept, dp))
+            F[j + base + kept] = e;
         }
         if (contrib) offset_add(d, in, e, c1 * ru * (wb - 0.0), epoch);
       }
@@ -280,21 +287,46 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
   }
 }
 
-// In-lists longer than kHubThreshold are summed in pieces by the pull step.
-__global__ void k_hubs(Dev d) {
+// Fold the batch's edge-count change into m.
+__global__ void k_merge_finish(Dev d) {
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  ctl->m += ctl->m_delta;
+  ctl->m_delta = 0;
+  ctl->n_hubs = 0;
+}
+
+// Pull-step plan, part 1: warp task t starts at the first node v with
+// pc[v] + v >= t * kTaskItems (so a task holds about kTaskItems edges + nodes
+// and never splits a list); long in-lists are listed for piecewise summation.
+__global__ void k_pull_plan(Dev d) {
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   const int n = ctl->n;
+  const long long W = (long long)n + ctl->m;
+  const int nt = (int)((W + kTaskItems - 1) / kTaskItems);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  if (tid == 0) ctl->n_tasks = nt;
+  for (int t = tid; t <= nt; t += nth) {
+    const long long target = (long long)t * kTaskItems;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((long long)d.pc[mid] + mid < target) lo = mid + 1;
+      else hi = mid;
+    }
+    d.task_first[t] = t == nt ? n : lo;
+  }
   const int lane = threadIdx.x & 31;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += nth) {
     const int v = base + lane;
     const bool h = v < n && d.len_c[v] > kHubThreshold;
     warp_append(h, v, d.hubs, &ctl->n_hubs);
   }
 }
 
-// Piece prefix over the hub list; also folds the batch's edge-count change into m.
+// Pull-step plan, part 2 (one CTA): piece prefix over the long in-lists.
 __global__ void __launch_bounds__(1024) k_hub_prefix(Dev d) {
   __shared__ int s_w[32];
   Ctl* ctl = d.ctl;
@@ -331,8 +363,6 @@ __global__ void __launch_bounds__(1024) k_hub_prefix(Dev d) {
   if (tid == 0) {
     d.hub_pstart[nh] = s_w[31];
     ctl->n_pieces = s_w[31];
-    ctl->m += ctl->m_delta;
-    ctl->m_delta = 0;
   }
 }
 
@@ -454,8 +484,14 @@ __global__ void k_abs_sum(const double* __restrict__ r, int n, double* out) {
   }
 }
 
-__global__ void k_scale_copy(const double* __restrict__ r, int n, const double* __restrict__ sum,
+// Scores in caller order: out[x] = r[ext2int[x]].
+__global__ void k_gather_ext(const double* __restrict__ r, const int* __restrict__ ext2int, int n,
                              double* out) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+    out[x] = r[ext2int[x]];
+}
+
+__global__ void k_scale_copy(const double* r, int n, const double* __restrict__ sum, double* out) {
   const double s = *sum;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     out[i] = s > 0.0 ? r[i] / s : 0.0;

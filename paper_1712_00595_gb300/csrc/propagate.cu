@@ -9,9 +9,10 @@
 //         out-neighbours (atomic adds into xacc, first touch appends to the
 //         next frontier); an epilogue over the new frontier adds x(i) into r,
 //         forms y(i) and sums |x(i)|.
-//   pull: x(i) is dense. Each node v sums y(i-1) over its in-list (one lane
-//         per short list, a warp per longer list, several warps per hub list)
-//         and the same pass adds x(i) into r, writes y(i) and sums |x(i)|.
+//   pull: x(i) is dense. Each node v sums y(i-1) over its in-list and the
+//         same pass adds x(i) into r, writes y(i) and sums |x(i)|. CTAs own
+//         node ranges of equal work (edges + nodes); long lists are summed in
+//         pieces by all warps.
 // The step switches to pull once the frontier's out-edges exceed m / alpha or
 // its size exceeds n / beta, and stays there. Between steps a grid barrier
 // (bounded wait) reduces the per-CTA |x| partials in a fixed order and takes
@@ -133,11 +134,15 @@ __device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n,
   if (step_mode < 0) {  // x(0)
     it = 0;
     d.l1_hist[0] = L1;
+    d.step_ns[1] = global_ns();
     stop = 0;  // at least one step always runs
   } else {
     it = ctl->iter + 1;
     ctl->iter = it;
-    if (it < kMaxHist) d.l1_hist[it] = L1;
+    if (it < kMaxHist) {
+      d.l1_hist[it] = L1;
+      d.step_ns[it + 1] = global_ns();
+    }
     if (step_mode == kPush) {
       ctl->visited += ctl->ef;
       ctl->push_iters += 1;
@@ -176,7 +181,7 @@ __device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n,
 
 template <typename T>
 __device__ void push_scatter(const Dev& d, const int* qsrc, int qs, T* ys, int* qdst,
-                             int* qdst_size, int ep, int* ctr) {
+                             int* qdst_size, int ep, int* ctr, int* big_count) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int t = 0;
@@ -186,7 +191,8 @@ __device__ void push_scatter(const Dev& d, const int* qsrc, int qs, T* ys, int* 
     if (i0 >= qs) break;
     const int i = i0 + lane;
     const bool valid = i < qs;
-    const int u = valid ? __ldcg(qsrc + i) : 0;
+    int u = valid ? __ldcg(qsrc + i) : 0;
+    if (!OSP_GUARD(d.ctl, u >= 0 && u < d.nc, "push frontier id", i, u, qs)) u = 0;
     T val = (T)0;
     if (valid) {
       val = __ldcg(ys + u);
@@ -203,12 +209,31 @@ __device__ void push_scatter(const Dev& d, const int* qsrc, int qs, T* ys, int* 
     const int maxl = warp_max(ll);
     for (int j = 0; j < maxl; ++j) {
       const bool act = j < ll;
-      const int v = act ? __ldg(d.pool_r + o + j) : 0;
-      if (act) atomicAdd(&d.xacc[v], (double)val);
-      const bool need = act && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
+      int v = act ? __ldg(d.pool_r + o + j) : 0;
+      const bool okv = !act || OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "push light target", u, j, v);
+      const bool act2 = act && okv;
+      if (!okv) v = 0;
+      if (act2) atomicAdd(&d.xacc[v], (double)val);
+      const bool need = act2 && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
       warp_append(need, v, qdst, qdst_size);
     }
-    unsigned hm = __ballot_sync(0xffffffffu, !light);
+    // rows above kHubThreshold are scattered in pieces by all warps afterwards
+    const bool big = len > kHubThreshold;
+    {
+      const unsigned bm = __ballot_sync(0xffffffffu, big);
+      if (bm) {
+        int at = 0;
+        const int leader = __ffs(bm) - 1;
+        if (lane == leader) at = atomicAdd(big_count, __popc(bm));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (big) {
+          const int slot = at + __popc(bm & lanemask_lt());
+          d.big_u[slot] = u;
+          d.big_y[slot] = (double)val;
+        }
+      }
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, !light && !big);
     while (hm) {
       const int l = __ffs(hm) - 1;
       hm &= hm - 1;
@@ -218,69 +243,76 @@ __device__ void push_scatter(const Dev& d, const int* qsrc, int qs, T* ys, int* 
       for (int b = 0; b < hl; b += 32) {
         const int j = b + lane;
         const bool act = j < hl;
-        const int v = act ? __ldg(d.pool_r + ho + j) : 0;
-        if (act) atomicAdd(&d.xacc[v], (double)hv);
-        const bool need = act && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
+        int v = act ? __ldg(d.pool_r + ho + j) : 0;
+        const bool okv = !act || OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "push heavy target", ho, j, v);
+        const bool act2 = act && okv;
+        if (!okv) v = 0;
+        if (act2) atomicAdd(&d.xacc[v], (double)hv);
+        const bool need = act2 && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
         warp_append(need, v, qdst, qdst_size);
       }
     }
   }
 }
 
-template <typename T>
-__device__ double pull_step(const Dev& d, int n, const T* ys, T* yd, const T* __restrict__ scale,
-                            int n_hubs, int n_pieces, int* ctr_hub) {
-  double l1 = 0.0;
+// Pieces of the push rows longer than kHubThreshold, spread over all warps.
+__device__ void push_big_rows(const Dev& d, int nb, int* qdst, int* qdst_size, int ep) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  const int nchunks = (n + 31) >> 5;
-  for (int t = gw; t < nchunks; t += nw) {
-    const int v = (t << 5) + lane;
-    const bool valid = v < n;
-    unsigned o = 0;
-    int len = 0;
-    if (valid) {
-      o = __ldg(d.off_c + v);
-      len = __ldg(d.len_c + v);
-    }
-    const bool hub = len > kHubThreshold;
-    const bool light = len <= kLight;
-    T s = (T)0;
-    if (light) {
-      const int* p = d.pool_c + o;
-      int j = 0;
-      for (; j + 4 <= len; j += 4) {
-        const int a0 = __ldg(p + j), a1 = __ldg(p + j + 1), a2 = __ldg(p + j + 2),
-                  a3 = __ldg(p + j + 3);
-        s += (ys[a0] + ys[a1]) + (ys[a2] + ys[a3]);
+  int base = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int u = __ldcg(d.big_u + b);
+    const double val = __ldcg(d.big_y + b);
+    const unsigned o = __ldg(d.off_r + u);
+    const int len = __ldg(d.len_r + u);
+    const int np = (len + kHubPiece - 1) / kHubPiece;
+    for (int q = ((gw - base) % nw + nw) % nw; q < np; q += nw) {
+      const int j0 = q * kHubPiece, j1 = min(len, j0 + kHubPiece);
+      for (int jb = j0; jb < j1; jb += 32) {
+        const int j = jb + lane;
+        const bool act = j < j1;
+        int v = act ? __ldg(d.pool_r + o + j) : 0;
+        const bool okv = !act || OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "push big target", u, j, v);
+        const bool act2 = act && okv;
+        if (!okv) v = 0;
+        if (act2) atomicAdd(&d.xacc[v], val);
+        const bool need = act2 && d.mark[v] != ep && atomicExch(&d.mark[v], ep) != ep;
+        warp_append(need, v, qdst, qdst_size);
       }
-      for (; j < len; ++j) s += ys[__ldg(p + j)];
     }
-    unsigned hm = __ballot_sync(0xffffffffu, !light && !hub);
-    while (hm) {
-      const int l = __ffs(hm) - 1;
-      hm &= hm - 1;
-      const unsigned ho = __shfl_sync(0xffffffffu, o, l);
-      const int hl = __shfl_sync(0xffffffffu, len, l);
-      T p = (T)0;
-      for (int j = lane; j < hl; j += 32) p += ys[__ldg(d.pool_c + ho + j)];
-      p = warp_sum(p);
-      if (lane == l) s = p;
-    }
-    if (valid && !hub) {
-      const double x = (double)s;
-      d.r[v] += x;
-      l1 += fabs(x);
-      yd[v] = s * __ldg(scale + v);
-    }
+    base += np;
   }
-  // hub lists, split into pieces; the piece that completes a hub finishes it
-  for (;;) {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(ctr_hub, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n_pieces) break;
+}
+
+__device__ __forceinline__ void finish_node(const Dev& d, int v, double x, void* yd, bool fp32,
+                                            double& l1) {
+  if (!OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "finish node", v, 0, 0)) return;
+  d.r[v] += x;
+  l1 += fabs(x);
+  if (fp32) ((float*)yd)[v] = (float)x * __ldg(d.scale_f + v);
+  else ((double*)yd)[v] = x * __ldg(d.scale_d + v);
+}
+
+// Dense step. Warp tasks of about kTaskItems edges + nodes (planned per batch,
+// lists never split) are dealt round-robin to the warps; a task is walked 32
+// consecutive nodes at a time. The short in-lists of such a chunk are summed as
+// one flattened, coalesced stream of edges (segmented warp scan, four rounds
+// of 32 edges with their loads in flight), a longer list by the whole warp
+// with eight coalesced loads and gathers in flight per lane, and a list above
+// kHubThreshold is cut into pieces dealt to all warps before the chunks (the
+// piece that completes a list finishes it).
+template <typename T>
+__device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_pieces,
+                            int n_tasks, T* wacc) {
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  double l1 = 0.0;
+  const int lane = threadIdx.x & 31;
+  // long in-lists first, in pieces dealt round-robin to the warps, so that the
+  // end of the step is made of short chunks
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int t = gw; t < n_pieces; t += nw) {
     int lo = 0, hi = n_hubs;  // largest h with hub_pstart[h] <= t
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
@@ -291,13 +323,19 @@ __device__ double pull_step(const Dev& d, int n, const T* ys, T* yd, const T* __
     const int v = __ldg(d.hubs + h);
     const int piece = t - __ldg(d.hub_pstart + h);
     const int full = __ldg(d.len_c + v);
-    const unsigned o = __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
+    const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
     const int L = min(kHubPiece, full - piece * kHubPiece);
-    T p = (T)0;
-    for (int j = lane; j < L; j += 32) p += ys[__ldg(d.pool_c + o + j)];
-    p = warp_sum(p);
+    T acc = (T)0;
+    int j = lane;
+    for (; j + 96 < L; j += 128) {
+      const int a0 = __ldg(p + j), a1 = __ldg(p + j + 32), a2 = __ldg(p + j + 64),
+                a3 = __ldg(p + j + 96);
+      acc += (ys[a0] + ys[a1]) + (ys[a2] + ys[a3]);
+    }
+    for (; j < L; j += 32) acc += ys[__ldg(p + j)];
+    acc = warp_sum(acc);
     if (lane == 0) {
-      atomicAdd(&d.hub_acc[h], (double)p);
+      atomicAdd(&d.hub_acc[h], (double)acc);
       __threadfence();
       const int np = (full + kHubPiece - 1) / kHubPiece;
       if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
@@ -305,10 +343,101 @@ __device__ double pull_step(const Dev& d, int n, const T* ys, T* yd, const T* __
         const double x =
             __longlong_as_double((long long)atomicExch((unsigned long long*)&d.hub_acc[h], 0ull));
         d.hub_cnt[h] = 0;
-        d.r[v] += x;
-        l1 += fabs(x);
-        yd[v] = (T)(x * __ldg(d.scale_d + v));
+        finish_node(d, v, x, yd, kF32, l1);
       }
+    }
+  }
+  for (int t = gw; t < n_tasks; t += nw) {
+    const int c0 = __ldg(d.task_first + t), c1 = __ldg(d.task_first + t + 1);
+    for (int vb = c0; vb < c1; vb += 32) {
+      const int v = vb + lane;
+      const bool valid = v < c1;
+      unsigned o = 0;
+      int len = 0;
+      if (valid) {
+        o = __ldg(d.off_c + v);
+        len = __ldg(d.len_c + v);
+      }
+      const bool hub = len > kHubThreshold;
+      const bool light = len <= kLight;
+      // the chunk's short lists as one flattened edge stream: 32 consecutive
+      // edges per round, coalesced index loads; edge e belongs to the lane l
+      // with P_l <= e < P_l + len_l (P = exclusive prefix of the lengths)
+      const int ll = light ? len : 0;
+      int P = ll;
+  #pragma unroll
+      for (int q = 1; q < 32; q <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, P, q);
+        if (lane >= q) P += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, P, 31);
+      P -= ll;
+      wacc[lane] = (T)0;
+      __syncwarp();
+      constexpr int R = 4;  // rounds of 32 edges with their loads in flight together
+      for (int eb = 0; eb < total; eb += 32 * R) {
+        int li[R];
+        unsigned addr[R];
+  #pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int e = eb + 32 * r + lane;
+          int lo = 0;  // largest lane with P <= e (lanes with empty lists share P with the next)
+  #pragma unroll
+          for (int q = 16; q > 0; q >>= 1) {
+            const int pm = __shfl_sync(0xffffffffu, P, lo + q);
+            if (pm <= e) lo += q;
+          }
+          const unsigned ob = __shfl_sync(0xffffffffu, o, lo);
+          const int pb = __shfl_sync(0xffffffffu, P, lo);
+          li[r] = e < total ? lo : -1;
+          addr[r] = ob + (unsigned)(e - pb);
+        }
+  #pragma unroll
+        for (int r = 0; r < R; ++r) addr[r] = li[r] >= 0 ? __ldg(d.pool_c + addr[r]) : 0u;
+        T val[R];
+  #pragma unroll
+        for (int r = 0; r < R; ++r) val[r] = li[r] >= 0 ? ys[addr[r]] : (T)0;
+  #pragma unroll
+        for (int r = 0; r < R; ++r) {
+          T v = val[r];
+          const int prev = __shfl_up_sync(0xffffffffu, li[r], 1);
+          const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != li[r]);
+          const int seg0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  #pragma unroll
+          for (int q = 1; q < 32; q <<= 1) {
+            const T t = __shfl_up_sync(0xffffffffu, v, q);
+            if (lane - q >= seg0) v += t;
+          }
+          const int nxt = __shfl_down_sync(0xffffffffu, li[r], 1);
+          if (li[r] >= 0 && (lane == 31 || nxt != li[r])) wacc[li[r]] += v;  // one tail per list
+          __syncwarp();
+        }
+      }
+      T s = wacc[lane];
+      // longer lists: the whole warp, eight coalesced loads and gathers in flight per lane
+      unsigned hm = __ballot_sync(0xffffffffu, !light && !hub);
+      while (hm) {
+        const int l = __ffs(hm) - 1;
+        hm &= hm - 1;
+        const int* p = d.pool_c + __shfl_sync(0xffffffffu, o, l);
+        const int hl = __shfl_sync(0xffffffffu, len, l);
+        T acc = (T)0;
+        for (int jb = 0; jb < hl; jb += 256) {
+          int a[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int j = jb + 32 * q + lane;
+            a[q] = j < hl ? __ldg(p + j) : -1;
+          }
+          T t[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) t[q] = a[q] >= 0 ? ys[a[q]] : (T)0;
+          acc += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+        }
+        acc = warp_sum(acc);
+        if (lane == l) s = acc;
+      }
+      if (valid && !hub) finish_node(d, v, (double)s, yd, kF32, l1);
     }
   }
   return l1;
@@ -321,6 +450,7 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
   __shared__ BarShared sh;
   __shared__ double s_l1[kPropWarps];
   __shared__ long long s_ef[kPropWarps];
+  __shared__ T s_wacc[kPropThreads];  // per-warp accumulators of the short-list stream
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   const int n = ctl->n;
@@ -328,20 +458,22 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
   const int epoch = ctl->epoch;
   const int n_hubs = ctl->n_hubs;
   const int n_pieces = ctl->n_pieces;
+  const int n_tasks = ctl->n_tasks;
   T* yb[2] = {(T*)d.y0, (T*)d.y1};
   int* qb[2] = {d.q0, d.q1};
-  const T* scale = (const T*)(std::is_same<T, float>::value ? (const void*)d.scale_f
-                                                             : (const void*)d.scale_d);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthreads = gridDim.x * blockDim.x;
+  if (tid == 0) d.step_ns[0] = global_ns();
 
   // x(0) (the offset vector, or c e_s for CPI) sits in xacc over queue 0
   {
     double l1 = 0.0;
     long long ef = 0;
     const int qs = *(volatile int*)&ctl->q_size[0];
+    if (!OSP_GUARD(ctl, qs >= 0 && qs <= d.nc, "first frontier size", qs, 0, 0)) return;
     for (int k = tid; k < qs; k += nthreads) {
       const int v = __ldcg(d.q0 + k);
+      if (!OSP_GUARD(ctl, v >= 0 && v < d.nc, "first frontier id", k, v, qs)) continue;
       const double x = __ldcg(d.xacc + v);
       d.xacc[v] = 0.0;
       d.r[v] += x;
@@ -363,14 +495,20 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
     if (mode == kPush) {
       const int qs = *(volatile int*)&ctl->q_size[src];
       push_scatter<T>(d, qb[src], qs, yb[src], qb[dst], &ctl->q_size[dst], epoch + it,
-                      &ctl->ctr[0]);
-      if (bar_arrive(ctl, sh) && threadIdx.x == 0)
-        for (int i = 0; i < 4; ++i) ctl->ctr[i] = 0;
+                      &ctl->ctr[0], &ctl->ctr[2]);
+      if (bar_arrive(ctl, sh) && threadIdx.x == 0) ctl->ctr[0] = 0;
       if (!bar_release(ctl, sh)) return;
+      const int nbig = *(volatile int*)&ctl->ctr[2];
+      if (nbig > 0) {  // uniform: every CTA read the same count after the barrier
+        push_big_rows(d, nbig, qb[dst], &ctl->q_size[dst], epoch + it);
+        if (bar_arrive(ctl, sh) && threadIdx.x == 0) ctl->ctr[2] = 0;
+        if (!bar_release(ctl, sh)) return;
+      }
       const int qn = *(volatile int*)&ctl->q_size[dst];
       T* yd = yb[dst];
       for (int k = tid; k < qn; k += nthreads) {
         const int v = __ldcg(qb[dst] + k);
+        if (!OSP_GUARD(ctl, v >= 0 && v < d.nc && qn <= d.nc, "frontier id", k, v, qn)) continue;
         const double x = __ldcg(d.xacc + v);
         d.xacc[v] = 0.0;
         d.r[v] += x;
@@ -379,7 +517,8 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
         ef += __ldg(d.len_r + v);
       }
     } else {
-      l1 = pull_step<T>(d, n, yb[src], yb[dst], scale, n_hubs, n_pieces, &ctl->ctr[1]);
+      l1 = pull_step<T>(d, yb[src], yb[dst], n_hubs, n_pieces, n_tasks,
+                        s_wacc + (threadIdx.x & ~31));
     }
     block_partials(d, l1, ef, s_l1, s_ef);
     if (bar_arrive(ctl, sh)) decide(d, pp, mode, n, m, s_l1, s_ef);

@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libosp_gb300.so")
+# OSP_LIBRARY selects another build of the same ABI (e.g. the bounds-checked one).
+LIB_PATH = os.environ.get("OSP_LIBRARY") or os.path.join(HERE, "_build", "libosp_gb300.so")
 
 OSP_OK, OSP_EINVAL, OSP_ENOMEM, OSP_ECUDA, OSP_ETIMEOUT, OSP_ENOCONV, OSP_ESTATE, OSP_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6, -7)
@@ -25,14 +26,15 @@ EXPORTED = [
     "osp_default_options", "osp_create", "osp_destroy", "osp_load_graph", "osp_set_seeds",
     "osp_init_scores", "osp_apply_updates", "osp_apply_updates_device", "osp_max_batch",
     "osp_query", "osp_query_device", "osp_topk", "osp_export_graph", "osp_get_size",
-    "osp_get_l1_history", "osp_set_fixed_iterations", "osp_last_error", "osp_status_string",
+    "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
+    "osp_status_string",
 ]
 
 
 class osp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("max_nodes", C.c_int64), ("push_alpha", C.c_double), ("push_beta", C.c_double),
-                ("max_iter", C.c_int32), ("reserved", C.c_int32)]
+                ("max_iter", C.c_int32), ("node_order", C.c_int32)]
 
 
 class osp_batch_stats(C.Structure):
@@ -42,7 +44,8 @@ class osp_batch_stats(C.Structure):
                 ("net_inserts", C.c_int64), ("net_deletes", C.c_int64),
                 ("changed_rows", C.c_int64), ("bad_op", C.c_int64),
                 ("push_frontier", C.c_int64), ("push_reached", C.c_int64),
-                ("ms_update", C.c_float), ("ms_propagate", C.c_float)]
+                ("ms_update", C.c_float), ("ms_propagate", C.c_float),
+                ("kernel_launches", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +87,7 @@ def load_library(path: str = LIB_PATH):
             "osp_export_graph": (C.c_int, [P, C.c_int, P, P]),
             "osp_get_size": (C.c_int, [P, P, P]),
             "osp_get_l1_history": (C.c_int, [P, P, i32, P]),
+            "osp_get_step_times": (C.c_int, [P, P, i32, P]),
             "osp_set_fixed_iterations": (C.c_int, [P, i32]),
             "osp_last_error": (C.c_char_p, [P]),
             "osp_status_string": (C.c_char_p, [C.c_int]),
@@ -116,7 +120,7 @@ class Engine:
     """One engine context (osp_ctx). Methods mirror the C ABI one to one."""
 
     def __init__(self, precision=OSP_PREC_FP32_ACC64, device=0, stream=None, max_nodes=0,
-                 push_alpha=0.0, push_beta=0.0, max_iter=0):
+                 push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0):
         L = load_library()
         opt = osp_options()
         L.osp_default_options(C.byref(opt))
@@ -127,6 +131,7 @@ class Engine:
         opt.push_alpha = push_alpha
         opt.push_beta = push_beta
         opt.max_iter = max_iter
+        opt.node_order = node_order
         h = C.c_void_p()
         s = L.osp_create(C.byref(h), C.byref(opt))
         if s != OSP_OK:
@@ -217,6 +222,13 @@ class Engine:
         out = np.empty(cap, np.float64)
         cnt = C.c_int32(0)
         self._check(self._L.osp_get_l1_history(self._h, _ptr(out), int(cap), C.byref(cnt)))
+        return out[: cnt.value]
+
+    def get_step_times(self, cap=4096):
+        """Microseconds of the x(0) pass and of each propagation step of the last call."""
+        out = np.empty(cap, np.float64)
+        cnt = C.c_int32(0)
+        self._check(self._L.osp_get_step_times(self._h, _ptr(out), int(cap), C.byref(cnt)))
         return out[: cnt.value]
 
     def set_fixed_iterations(self, k):

@@ -118,14 +118,15 @@ def mixed_sequence(rng, n, src, dst, batches, n_ops, seed=0):
     return out
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("prec", PRECS)
-def test_osp_sequence_with_all_op_kinds(prec):
+def test_osp_sequence_with_all_op_kinds(prec, order):
     rng = np.random.default_rng(40 + prec)
     n = 400
     src, dst = hub_graph(rng, n=n, m=3000, hub_in=300, hub_out=200, mids=5)
     batches = mixed_sequence(rng, n, src, dst, 6, 150)
     eps = 1e-12
-    eng, _ = engine(prec, n, src, dst, eps_init=eps, max_nodes=n + 4096)
+    eng, _ = engine(prec, n, src, dst, eps_init=eps, max_nodes=n + 4096, node_order=order)
     g = O.Graph(n, src, dst)
     cur = g.csr()
     r_o, _, _ = O.cpi(*cur, 0, C_RESTART, eps)
@@ -366,7 +367,8 @@ def test_rmat20_bench_configuration_sampled():
         e.close()
 
 
-def test_topk_matches_ranking_of_the_score_vector():
+@pytest.mark.parametrize("order", [0, 1])
+def test_topk_matches_ranking_of_the_score_vector(order):
     rng = np.random.default_rng(8)
     # star with 700 equal-score leaves (ties), unreachable nodes (zero scores), random part
     n = 3000
@@ -378,7 +380,7 @@ def test_topk_matches_ranking_of_the_score_vector():
     keep = src != dst
     src, dst = src[keep], dst[keep]
     for seed in (0, 5):
-        eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, seed=seed, eps_init=1e-13)
+        eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, seed=seed, eps_init=1e-13, node_order=order)
         r = eng.query()
         for k in (1, 10, 100, 701, 1000, 4096):
             ids, sc = eng.topk(k)
