@@ -22,12 +22,14 @@ OSP_OK, OSP_EINVAL, OSP_ENOMEM, OSP_ECUDA, OSP_ETIMEOUT, OSP_ENOCONV, OSP_ESTATE
 OSP_PREC_FP64, OSP_PREC_FP32_ACC64 = 0, 1
 UPDATE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("op", "<i4")])
 
+TOPK_NOALLOC_MAX_N = 16777216  # OSP_TOPK_NOALLOC_MAX_N
+
 EXPORTED = [
     "osp_default_options", "osp_create", "osp_destroy", "osp_load_graph", "osp_set_seeds",
     "osp_init_scores", "osp_apply_updates", "osp_apply_updates_device", "osp_max_batch",
     "osp_query", "osp_query_device", "osp_topk", "osp_export_graph", "osp_get_size",
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
-    "osp_status_string",
+    "osp_status_string", "osp_topk_noalloc",
 ]
 
 
@@ -91,6 +93,7 @@ def load_library(path: str = LIB_PATH):
             "osp_set_fixed_iterations": (C.c_int, [P, i32]),
             "osp_last_error": (C.c_char_p, [P]),
             "osp_status_string": (C.c_char_p, [C.c_int]),
+            "osp_topk_noalloc": (C.c_int, [P, i64, i32, C.c_int, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -114,6 +117,21 @@ def _ptr(a) -> C.c_void_p:
     if isinstance(a, int):
         return C.c_void_p(a)
     return a.ctypes.data_as(C.c_void_p)
+
+
+def topk_noalloc(scores_device, n, k, ids_device, out_scores_device, k_out_device,
+                 normalize=False, stream=None):
+    """osp_topk_noalloc on device buffers (tensors or raw pointers) of the
+    current device; asynchronous on `stream` (a raw cudaStream_t or None)."""
+    L = load_library()
+    s = L.osp_topk_noalloc(_ptr(scores_device), int(n), int(k), int(bool(normalize)),
+                           _ptr(ids_device), _ptr(out_scores_device), _ptr(k_out_device),
+                           _ptr(stream) if stream is not None else None)
+    if s == OSP_EINVAL:
+        raise OspError(s, "osp_topk_noalloc: n must lie in [0, %d], k in [1, 4096], every "
+                          "pointer non-null, device ordinal <= 63" % TOPK_NOALLOC_MAX_N)
+    if s != 0:
+        raise OspError(s, "osp_topk_noalloc: CUDA call or launch failed")
 
 
 class Engine:
