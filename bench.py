@@ -53,11 +53,16 @@ def parse():
     p.add_argument("--eps", type=float, default=1e-6)
     p.add_argument("--eps-init", type=float, default=1e-10)
     p.add_argument("--no-extras", action="store_true", help="headline only (profiling runs)")
-    p.add_argument("--cpu-sample", type=int, default=3, help="oracle batches timed for cpu_baseline")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="CPU time bound of the cpu_baseline sample (whole batches)")
     return p.parse_args()
 
 
+STREAM_MIN_BATCHES = 64  # both arms draw the same stream (its batches depend on its length)
+
+
 def make_workload(scale, batches):
+    batches = max(batches, STREAM_MIN_BATCHES)
     gen, src, dst = W.rmat_graph(scale, 16 << scale, seed=W.BASE_SEED + HUB_SEED_OFFSET)
     n = gen.n
     seed = W.max_out_degree_seed(n, src)
@@ -245,18 +250,20 @@ def workload_config(args, n, m, seed, precision):
 
 
 def cpu_baseline(args, n, src, dst, seed, stream):
-    """The oracle as it stands on a bounded sample: cpu_sample batches after its own CPI."""
+    """The oracle as it stands on a bounded sample: whole batches, after its own CPI,
+    until --cpu-seconds have passed."""
     from oracle import oracle as O
     g = O.Graph(n, src, dst)
     cur = g.csr()
     r, _, _ = O.cpi(*cur, seed, C_RESTART, args.eps_init)
-    k = max(1, args.cpu_sample)
+    k = 0
     t0 = time.perf_counter()
-    for b in range(k):
-        assert g.apply(stream[b], protect=(seed,)) == -1
+    while k < len(stream) and (k == 0 or time.perf_counter() - t0 < args.cpu_seconds):
+        assert g.apply(stream[k], protect=(seed,)) == -1
         new = g.csr()
         r, _, _, _ = O.osp(cur, new, r, C_RESTART, args.eps)
         cur = new
+        k += 1
     dt = time.perf_counter() - t0
     return {"value": k / dt, "unit": "batches/s", "cores": 1, "kind": "oracle",
             "sample": "first %d batches of the same stream (graph update + Algorithm 1, FP64, "

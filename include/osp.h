@@ -85,9 +85,9 @@ typedef struct {
     double push_alpha;  /* sparse (push) steps while frontier out-edges <= m / alpha (0 = 14) */
     double push_beta;   /* ... and frontier size <= n / beta (0 = 24) */
     int32_t max_iter;   /* iteration cap; 0 = ceil(log_{1-c}(eps/2)) + 8 (Theorem 3) */
-    int32_t node_order; /* internal node order: 0 = descending out-degree of the loaded graph
-                           (locality of the gathers), 1 = the caller's ids. Results are the
-                           same up to rounding order; every call uses the caller's ids. */
+    int32_t node_order; /* internal node order: 0 = the caller's ids, 1 = descending
+                           out-degree of the loaded graph. Results are the same up to
+                           rounding order; every call uses the caller's ids. */
 } osp_options;
 
 /* Per-call statistics (the columns of Table 2 plus bookkeeping). */

@@ -523,10 +523,10 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   build_lists(n, a, b, off_r, len_r, pool_r);
   build_lists(n, b, a, off_c, len_c, pool_c);
   const int64_t mm = (int64_t)pool_r.size();
-  // internal order: descending out-degree (ties by id), or the caller's ids
+  // internal order: the caller's ids, or descending out-degree (ties by id)
   std::vector<int32_t> i2e(n), e2i(n);
   for (int64_t i = 0; i < n; ++i) i2e[i] = (int32_t)i;
-  if (ctx->opt.node_order == 0)
+  if (ctx->opt.node_order == 1)
     std::stable_sort(i2e.begin(), i2e.end(),
                      [&](int32_t x, int32_t y) { return len_r[x] > len_r[y]; });
   for (int64_t i = 0; i < n; ++i) e2i[i2e[i]] = (int32_t)i;

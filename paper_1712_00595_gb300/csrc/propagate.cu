@@ -304,51 +304,63 @@ __device__ __forceinline__ void finish_node(const Dev& d, int v, double x, void*
 // piece that completes a list finishes it).
 template <typename T>
 __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_pieces,
-                            int n_tasks, T* wacc) {
+                            int n_tasks, T* wacc, int* grab) {
   constexpr bool kF32 = std::is_same<T, float>::value;
   double l1 = 0.0;
   const int lane = threadIdx.x & 31;
-  // long in-lists first, in pieces dealt round-robin to the warps, so that the
-  // end of the step is made of short chunks
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int t = gw; t < n_pieces; t += nw) {
-    int lo = 0, hi = n_hubs;  // largest h with hub_pstart[h] <= t
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (__ldg(d.hub_pstart + mid) <= t) lo = mid;
-      else hi = mid;
-    }
-    const int h = lo;
-    const int v = __ldg(d.hubs + h);
-    const int piece = t - __ldg(d.hub_pstart + h);
-    const int full = __ldg(d.len_c + v);
-    const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
-    const int L = min(kHubPiece, full - piece * kHubPiece);
-    T acc = (T)0;
-    int j = lane;
-    for (; j + 96 < L; j += 128) {
-      const int a0 = __ldg(p + j), a1 = __ldg(p + j + 32), a2 = __ldg(p + j + 64),
-                a3 = __ldg(p + j + 96);
-      acc += (ys[a0] + ys[a1]) + (ys[a2] + ys[a3]);
-    }
-    for (; j < L; j += 32) acc += ys[__ldg(p + j)];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      atomicAdd(&d.hub_acc[h], (double)acc);
-      __threadfence();
-      const int np = (full + kHubPiece - 1) / kHubPiece;
-      if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
-        __threadfence();
-        const double x =
-            __longlong_as_double((long long)atomicExch((unsigned long long*)&d.hub_acc[h], 0ull));
-        d.hub_cnt[h] = 0;
-        finish_node(d, v, x, yd, kF32, l1);
+  // Work items 0 .. n_pieces-1 are pieces of the long in-lists, the rest the
+  // warp tasks; each warp takes the next item from a grid-wide counter, so the
+  // long lists go first and warps that finish early take more of the rest.
+  const int n_items = n_pieces + n_tasks;
+  // Tasks are taken in a scrambled order, t -> t * P mod n_tasks (P prime and
+  // coprime to n_tasks), so that the warps busy at any moment hold a mix of
+  // list lengths rather than one run of neighbouring (similar) nodes.
+  long long P = 7919;
+  if (n_tasks % 7919 == 0) P = 7907;
+  if (n_tasks % P == 0) P = 1;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(grab, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_items) break;
+    if (t < n_pieces) {
+      int lo = 0, hi = n_hubs;  // largest h with hub_pstart[h] <= t
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(d.hub_pstart + mid) <= t) lo = mid;
+        else hi = mid;
       }
+      const int h = lo;
+      const int v = __ldg(d.hubs + h);
+      const int piece = t - __ldg(d.hub_pstart + h);
+      const int full = __ldg(d.len_c + v);
+      const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
+      const int L = min(kHubPiece, full - piece * kHubPiece);
+      T acc = (T)0;
+      int j = lane;
+      for (; j + 96 < L; j += 128) {
+        const int a0 = __ldg(p + j), a1 = __ldg(p + j + 32), a2 = __ldg(p + j + 64),
+                  a3 = __ldg(p + j + 96);
+        acc += (ys[a0] + ys[a1]) + (ys[a2] + ys[a3]);
+      }
+      for (; j < L; j += 32) acc += ys[__ldg(p + j)];
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        atomicAdd(&d.hub_acc[h], (double)acc);
+        __threadfence();
+        const int np = (full + kHubPiece - 1) / kHubPiece;
+        if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
+          __threadfence();
+          const double x =
+              __longlong_as_double((long long)atomicExch((unsigned long long*)&d.hub_acc[h], 0ull));
+          d.hub_cnt[h] = 0;
+          finish_node(d, v, x, yd, kF32, l1);
+        }
+      }
+      continue;
     }
-  }
-  for (int t = gw; t < n_tasks; t += nw) {
-    const int c0 = __ldg(d.task_first + t), c1 = __ldg(d.task_first + t + 1);
+    const int task = (int)(((long long)(t - n_pieces) * P) % n_tasks);
+    const int c0 = __ldg(d.task_first + task), c1 = __ldg(d.task_first + task + 1);
     for (int vb = c0; vb < c1; vb += 32) {
       const int v = vb + lane;
       const bool valid = v < c1;
@@ -471,15 +483,32 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
     long long ef = 0;
     const int qs = *(volatile int*)&ctl->q_size[0];
     if (!OSP_GUARD(ctl, qs >= 0 && qs <= d.nc, "first frontier size", qs, 0, 0)) return;
-    for (int k = tid; k < qs; k += nthreads) {
-      const int v = __ldcg(d.q0 + k);
-      if (!OSP_GUARD(ctl, v >= 0 && v < d.nc, "first frontier id", k, v, qs)) continue;
-      const double x = __ldcg(d.xacc + v);
-      d.xacc[v] = 0.0;
-      d.r[v] += x;
-      l1 += fabs(x);
-      yb[0][v] = (T)(x * __ldg(d.scale_d + v));
-      ef += __ldg(d.len_r + v);
+    if ((double)qs > (double)n / pp.beta) {
+      // A frontier this large makes the next step a pull step whatever its edge
+      // count, so one coalesced pass over all nodes replaces the scattered walk
+      // of the queue (xacc is zero off the frontier; only nonzero entries count
+      // toward the edge total, which no decision reads in this case).
+      for (int v = tid; v < n; v += nthreads) {
+        const double x = __ldcg(d.xacc + v);
+        if (x != 0.0) {
+          d.xacc[v] = 0.0;
+          d.r[v] += x;
+          l1 += fabs(x);
+          yb[0][v] = (T)(x * __ldg(d.scale_d + v));
+          ef += __ldg(d.len_r + v);
+        }
+      }
+    } else {
+      for (int k = tid; k < qs; k += nthreads) {
+        const int v = __ldcg(d.q0 + k);
+        if (!OSP_GUARD(ctl, v >= 0 && v < d.nc, "first frontier id", k, v, qs)) continue;
+        const double x = __ldcg(d.xacc + v);
+        d.xacc[v] = 0.0;
+        d.r[v] += x;
+        l1 += fabs(x);
+        yb[0][v] = (T)(x * __ldg(d.scale_d + v));
+        ef += __ldg(d.len_r + v);
+      }
     }
     block_partials(d, l1, ef, s_l1, s_ef);
     if (bar_arrive(ctl, sh)) decide(d, pp, -1, n, m, s_l1, s_ef);
@@ -518,7 +547,7 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
       }
     } else {
       l1 = pull_step<T>(d, yb[src], yb[dst], n_hubs, n_pieces, n_tasks,
-                        s_wacc + (threadIdx.x & ~31));
+                        s_wacc + (threadIdx.x & ~31), &ctl->ctr[1]);
     }
     block_partials(d, l1, ef, s_l1, s_ef);
     if (bar_arrive(ctl, sh)) decide(d, pp, mode, n, m, s_l1, s_ef);
