@@ -28,6 +28,8 @@ constexpr int kPropWarps = kPropThreads / 32;
 constexpr int kHubThreshold = 1024;  // pull step: in-lists longer than this are summed in pieces
 constexpr int kHubPiece = 1024;      // pull step: edges per hub piece
 constexpr int kTaskItems = 1024;     // pull step: items (edges + nodes) per warp task
+constexpr double kPushAlpha = 14.0;  // push step while frontier out-edges <= m / alpha
+constexpr double kPushBeta = 24.0;   // ... and frontier size <= n / beta
 
 enum StepMode : int { kPush = 0, kPull = 1 };
 
@@ -47,7 +49,7 @@ struct Ctl {
   int n_hubs, n_pieces;        // pull step: long in-lists and their pieces
   int n_tasks;                 // pull step: warp tasks
   int n_mpieces;               // merge pieces of the current batch
-  int pad1;
+  int dense0;                  // 1: x(0) is found by a dense scan of xacc (no queue from the merge)
   int epoch;                   // frontier mark of x(0); step i uses epoch + i
   int q_size[2];               // frontier queue lengths
   unsigned int bar_count, bar_gen;

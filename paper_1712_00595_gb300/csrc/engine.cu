@@ -351,8 +351,8 @@ osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_
   pp.max_iter = default_max_iter(ctx, eps);
   pp.force_iters = ctx->fixed_iters;
   if (pp.force_iters > pp.max_iter) pp.max_iter = std::min(pp.force_iters, kMaxHist - 1);
-  pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : 14.0;
-  pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : 24.0;
+  pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : kPushAlpha;
+  pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : kPushBeta;
   pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
   osp_status s = plan_pull(ctx, n_bound, m_bound);
   if (s != OSP_OK) return s;
@@ -392,7 +392,8 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
   ++ctx->launches;
   k_expand<<<g, 256, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;
-  k_merge_pieces<<<1, 1024, 0, ctx->stream>>>(ctx->d);
+  k_merge_pieces<<<1, 1024, 0, ctx->stream>>>(
+      ctx->d, ctx->opt.push_beta > 0 ? ctx->opt.push_beta : kPushBeta);
   ++ctx->launches;
   k_merge_count<<<g, 256, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;

@@ -165,6 +165,7 @@ __global__ void k_reset_batch(Dev d) {
   c->n_del = 0;
   c->q_size[0] = 0;
   c->q_size[1] = 0;
+  c->dense0 = 0;
   for (int i = 0; i < 4; ++i) c->ctr[i] = 0;
   c->bar_count = 0;
   c->iter = 0;

@@ -8,7 +8,7 @@ __global__ void k_reset_batch(Dev d);
 __global__ void k_cpi_begin(Dev d);
 __global__ void k_ingest(Dev d, const osp_update* __restrict__ ops, int U);
 __global__ void k_expand(Dev d);
-__global__ void k_merge_pieces(Dev d);
+__global__ void k_merge_pieces(Dev d, double beta);
 __global__ void k_merge_count(Dev d);
 __global__ void k_merge_plan(Dev d);
 __global__ void k_merge_write(Dev d);

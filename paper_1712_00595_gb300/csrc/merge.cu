@@ -23,9 +23,13 @@
 namespace osp {
 namespace {
 
-__device__ __forceinline__ void offset_add(const Dev& d, bool want, int v, double val, int epoch) {
+// queue == false: the batch may touch more than n/beta nodes, and x(0) will be
+// found by a dense scan of xacc, so no mark or queue entry is made here.
+__device__ __forceinline__ void offset_add(const Dev& d, bool want, int v, double val, int epoch,
+                                           bool queue) {
   if (want && !OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "offset target", v, 0, 0)) want = false;
   if (want) atomicAdd(&d.xacc[v], val);
+  if (!queue) return;
   bool need = want && (d.mark[v] != epoch) && (atomicExch(&d.mark[v], epoch) != epoch);
   warp_append(need, v, d.q0, &d.ctl->q_size[0]);
 }
@@ -68,8 +72,9 @@ __device__ __forceinline__ ListRec list_rec(const Dev& d, int c, int n_rows) {
 }  // namespace
 
 // One CTA: list each changed list's pieces and remember its old slot.
-__global__ void __launch_bounds__(1024) k_merge_pieces(Dev d) {
+__global__ void __launch_bounds__(1024) k_merge_pieces(Dev d, double beta) {
   __shared__ int s_w[32];
+  __shared__ long long s_b[32];
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   const int nr = ctl->n_rec_r;
@@ -78,6 +83,7 @@ __global__ void __launch_bounds__(1024) k_merge_pieces(Dev d) {
   const int per = (R + 1023) / 1024;
   const int lo = min(R, tid * per), hi = min(R, lo + per);
   int mine = 0;
+  long long touch = 0;  // out-list entries old and new of the changed rows
   for (int c = lo; c < hi; ++c) {
     const bool rows = c < nr;
     const int node = rows ? d.rec_r_node[c] : d.rec_c_node[c - nr];
@@ -86,7 +92,10 @@ __global__ void __launch_bounds__(1024) k_merge_pieces(Dev d) {
     d.rec_old_off[c] = o;
     d.rec_old_len[c] = L;
     mine += L > 0 ? (L + kPiece - 1) / kPiece : 1;
+    if (rows) touch += L + d.rec_r_ic[c];
   }
+  touch = warp_sum(touch);
+  if (lane == 0) s_b[w] = touch;
   int x = mine;
   for (int o = 1; o < 32; o <<= 1) {
     int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -114,6 +123,11 @@ __global__ void __launch_bounds__(1024) k_merge_pieces(Dev d) {
   if (tid == 0) {
     ctl->n_mpieces = s_w[31];
     d.rec_pstart[R] = s_w[31];
+    long long t = 0;
+    for (int i = 0; i < 32; ++i) t += s_b[i];
+    // the offset reaches at most `t` nodes; above n/beta the first step is
+    // dense anyway and x(0) is collected by a scan instead of a queue
+    ctl->dense0 = (double)t > (double)ctl->n / beta;
   }
 }
 
@@ -124,6 +138,8 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
   const int np = ctl->n_mpieces, nr = ctl->n_rec_r;
   const double c1 = 1.0 - ctl->c;
   const int epoch = ctl->epoch;
+  const bool queue = !ctl->dense0;
+  const bool any_dead = ctl->n_del > 0;  // only nodes deleted by this batch still have edges
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
     const int q = p - d.rec_pstart[c];
     const unsigned o = d.rec_old_off[c];
     const int L = d.rec_old_len[c];
-    const bool cleared = d.dead[R.node];
+    const bool cleared = any_dead && d.dead[R.node];
     const double ru = R.rows ? d.r[R.node] : 0.0;
     const bool contrib = R.rows && ru != 0.0;
     const double wa = L ? 1.0 / (double)L : 0.0;
@@ -144,9 +160,10 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
       const bool in = i < L;
       int a = in ? R.pool[o + i] : 0;
       if (in && !OSP_GUARD(d.ctl, a >= 0 && a < d.nc, "merge count entry", c, i, a)) a = 0;
-      const bool keep = in && !cleared && !d.dead[a] && !contains_i(R.del + R.ds, R.dc, a);
+      const bool keep = in && !cleared && !(any_dead && d.dead[a]) &&
+                        !contains_i(R.del + R.ds, R.dc, a);
       cnt += __popc(__ballot_sync(0xffffffffu, keep));
-      if (contrib) offset_add(d, in && !keep, a, c1 * ru * (0.0 - wa), epoch);
+      if (contrib) offset_add(d, in && !keep, a, c1 * ru * (0.0 - wa), epoch, queue);
     }
     if (lane == 0) d.piece_cnt[p] = cnt;
   }
@@ -217,6 +234,8 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
   const int np = ctl->n_mpieces, nr = ctl->n_rec_r;
   const double c1 = 1.0 - ctl->c;
   const int epoch = ctl->epoch;
+  const bool queue = !ctl->dense0;
+  const bool any_dead = ctl->n_del > 0;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -232,7 +251,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
     const int base = d.piece_base[p];
     const int* I = R.ins + R.is;
     const int ic = R.ic;
-    const bool cleared = d.dead[R.node];
+    const bool cleared = any_dead && d.dead[R.node];
     const double ru = R.rows ? d.r[R.node] : 0.0;
     const bool contrib = R.rows && ru != 0.0;
     const double wa = L ? 1.0 / (double)L : 0.0;
@@ -246,7 +265,8 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
       const bool in = i < L;
       int a = in ? R.pool[o + i] : 0;
       if (in && !OSP_GUARD(d.ctl, a >= 0 && a < d.nc, "merge write entry", c, i, a)) a = 0;
-      const bool keep = in && !cleared && !d.dead[a] && !contains_i(R.del + R.ds, R.dc, a);
+      const bool keep = in && !cleared && !(any_dead && d.dead[a]) &&
+                        !contains_i(R.del + R.ds, R.dc, a);
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       masks[r] = m;
       if (keep) {
@@ -254,7 +274,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
         if (OSP_GUARD(d.ctl, pos >= 0 && pos < dp, "merge write position", c, pos, dp)) F[pos] = a;
       }
       run += __popc(m);
-      if (shift) offset_add(d, keep, a, c1 * ru * (wb - wa), epoch);
+      if (shift) offset_add(d, keep, a, c1 * ru * (wb - wa), epoch, queue);
     }
     // insertions that fall inside this piece of the old list
     if (ic > 0) {
@@ -281,7 +301,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
           if (OSP_GUARD(d.ctl, j + base + kept < dp, "merge insert position", c, j + base + kept, dp))
             F[j + base + kept] = e;
         }
-        if (contrib) offset_add(d, in, e, c1 * ru * (wb - 0.0), epoch);
+        if (contrib) offset_add(d, in, e, c1 * ru * (wb - 0.0), epoch, queue);
       }
     }
   }

@@ -146,8 +146,8 @@ __device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n,
     if (step_mode == kPush) {
       ctl->visited += ctl->ef;
       ctl->push_iters += 1;
-      ctl->push_f += ctl->q_size[(it + 1) & 1];
-      ctl->push_r += ctl->q_size[it & 1];
+      ctl->push_f += *(volatile int*)&ctl->q_size[(it + 1) & 1];
+      ctl->push_r += *(volatile int*)&ctl->q_size[it & 1];
     } else {
       ctl->visited += m;
       ctl->pull_used = 1;
@@ -168,7 +168,7 @@ __device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n,
   }
   int next = kPull;
   if (step_mode != kPull) {
-    const int qs = ctl->q_size[it & 1];
+    const int qs = *(volatile int*)&ctl->q_size[it & 1];
     const bool dense = (double)EF > (double)m / pp.alpha || (double)qs > (double)n / pp.beta;
     next = dense ? kPull : kPush;
   }
@@ -463,6 +463,8 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
   __shared__ double s_l1[kPropWarps];
   __shared__ long long s_ef[kPropWarps];
   __shared__ T s_wacc[kPropThreads];  // per-warp accumulators of the short-list stream
+  __shared__ int s_qw[kPropWarps];     // dense x(0) scan: queue offsets of the warps
+  __shared__ int s_qbase;
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   const int n = ctl->n;
@@ -483,20 +485,39 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
     long long ef = 0;
     const int qs = *(volatile int*)&ctl->q_size[0];
     if (!OSP_GUARD(ctl, qs >= 0 && qs <= d.nc, "first frontier size", qs, 0, 0)) return;
-    if ((double)qs > (double)n / pp.beta) {
-      // A frontier this large makes the next step a pull step whatever its edge
-      // count, so one coalesced pass over all nodes replaces the scattered walk
-      // of the queue (xacc is zero off the frontier; only nonzero entries count
-      // toward the edge total, which no decision reads in this case).
-      for (int v = tid; v < n; v += nthreads) {
-        const double x = __ldcg(d.xacc + v);
-        if (x != 0.0) {
+    if (*(volatile int*)&ctl->dense0) {
+      // The merge reached more than n/beta nodes and queued none of them: one
+      // coalesced pass over all nodes collects x(0) (xacc is zero off its
+      // support) and builds the frontier queue of its nonzero entries.
+      // One queue reservation per CTA tile of blockDim.x nodes (the loop is
+      // uniform over the CTA).
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      for (int base = blockIdx.x * blockDim.x; base < n; base += nthreads) {
+        const int v = base + threadIdx.x;
+        const double x = v < n ? __ldcg(d.xacc + v) : 0.0;
+        const bool nz = x != 0.0;
+        if (nz) {
           d.xacc[v] = 0.0;
           d.r[v] += x;
           l1 += fabs(x);
           yb[0][v] = (T)(x * __ldg(d.scale_d + v));
           ef += __ldg(d.len_r + v);
         }
+        const unsigned b = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) s_qw[w] = __popc(b);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int t = 0;
+          for (int i = 0; i < kPropWarps; ++i) {
+            const int c = s_qw[i];
+            s_qw[i] = t;
+            t += c;
+          }
+          s_qbase = t ? atomicAdd(&ctl->q_size[0], t) : 0;
+        }
+        __syncthreads();
+        if (nz) d.q0[s_qbase + s_qw[w] + __popc(b & lanemask_lt())] = v;
+        __syncthreads();
       }
     } else {
       for (int k = tid; k < qs; k += nthreads) {

@@ -148,6 +148,42 @@ def test_osp_sequence_with_all_op_kinds(prec, order):
     eng.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_dense_offset_scan_then_push_steps(prec):
+    """A batch whose changed rows could reach more than n/beta nodes makes the
+    merge skip the frontier queue and x(0) is found by a dense scan; when the
+    offset is in fact small (the long row belongs to a node with zero score) the
+    scan's queue must drive push steps."""
+    rng = np.random.default_rng(77)
+    n = 5000
+    src = rng.integers(0, 3000, 9000)
+    dst = rng.integers(0, 3000, 9000)
+    src = np.concatenate([src, [0, 0], np.full(1000, 4000)])  # 4000: unreachable, long row
+    dst = np.concatenate([dst, [1, 2], rng.choice(3000, 1000, replace=False)])
+    keep = src != dst
+    src, dst = src[keep].astype(np.int32), dst[keep].astype(np.int32)
+    eps = 1e-12
+    eng, _ = engine(prec, n, src, dst, eps_init=eps)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o, _, _ = O.cpi(*cur, 0, C_RESTART, eps)
+    assert r_o[4000] == 0.0
+    nbr = int(dst[src == 0][0])
+    for rows in ([(4000, 4500, 0), (0, 4999, 0)], [(4000, 4501, 0), (0, nbr, 1)]):
+        arr = np.empty(len(rows), W.UPDATE_DTYPE)
+        arr["u"], arr["v"], arr["op"] = np.array(rows).T
+        st = eng.apply_updates(arr, 1e-9)
+        assert g.apply(arr, protect=(0,)) == -1
+        new = g.csr()
+        force = st["iterations"]
+        r_o, q, ost, _ = O.osp(cur, new, r_o, C_RESTART, 1e-9, force_iters=force)
+        cur = new
+        assert st["push_iterations"] >= 1
+        assert st["qoff_l1"] == pytest.approx(np.abs(q).sum(), rel=1e-6, abs=1e-15)
+        assert l1(eng.query(), r_o) <= TOL[prec]
+    eng.close()
+
+
 def test_invalid_batches_rejected_state_unchanged():
     rng = np.random.default_rng(9)
     n = 50
