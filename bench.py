@@ -91,11 +91,22 @@ def alg_bytes(st, n, m, bx, bs):
     return pull + push
 
 
+TRAFFIC_SOURCES = ("propagate.cu", "common.cuh")
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the propagation kernel's sources."""
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1712_00595_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile():
     """Per-launch DRAM bytes of the propagation kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    summary, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "propagate_rmat20_traffic.txt")
-    src = os.path.join(ROOT, "paper_1712_00595_gb300", "csrc", "propagate.cu")
     try:
         vals = {}
         with open(path) as f:
@@ -103,9 +114,7 @@ def traffic_from_profile():
                 if "=" in line and not line.startswith("#"):
                     k, v = line.split("=", 1)
                     vals[k.strip()] = v.strip()
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
-        if vals.get("source_sha256_16") != h:
+        if vals.get("source_sha256_16") != kernel_source_hash():
             return None
         return float(vals["dram_bytes_per_launch"])
     except Exception:
@@ -144,9 +153,9 @@ class Clocks:
             self.proc.kill()
         self.fh.close()
         rows = list(csv.reader(open(self.path)))
-        out_dir = os.path.join(ROOT, "gpurun_out")
-        if os.path.isdir(out_dir):
-            with open(os.path.join(out_dir, "bench_clocks.csv"), "w") as f:
+        keep = os.environ.get("OSP_CLOCKS_LOG")  # optional copy of the raw samples
+        if keep:
+            with open(keep, "w") as f:
                 f.write(open(self.path).read())
         os.unlink(self.path)
         if len(rows) < 2:
