@@ -52,8 +52,17 @@ typedef enum {
  * FP64:        gather vector, products and every sum in double.
  * FP32_ACC64:  gather vector and products in float (in-row sums of the pull
  *              step in float); scores r, the offset vector, push-step
- *              accumulation and the ||x||_1 stopping test in double. */
-typedef enum { OSP_PREC_FP64 = 0, OSP_PREC_FP32_ACC64 = 1 } osp_precision;
+ *              accumulation and the ||x||_1 stopping test in double.
+ * BF16_ACC64:  batches store the gather vector as bfloat16 (rounded to
+ *              nearest), products and in-row sums in float, r / offset /
+ *              stopping test in double; osp_init_scores runs as FP32_ACC64.
+ *              Two or more seeds only (osp_set_seeds returns OSP_ENOTSUP for
+ *              one). */
+typedef enum {
+    OSP_PREC_FP64 = 0,
+    OSP_PREC_FP32_ACC64 = 1,
+    OSP_PREC_BF16_ACC64 = 2
+} osp_precision;
 
 /* One update. Operations of a batch apply in order (Sec. 3.4.1 for nodes).
  *  OSP_OP_INSERT_EDGE (u,v): add edge u->v; no-op if present.
@@ -127,12 +136,21 @@ void osp_destroy(osp_ctx *ctx);
 osp_status osp_load_graph(osp_ctx *ctx, int64_t n, int64_t m, const int32_t *src,
                           const int32_t *dst, int undirected);
 
-/* Set the seed node(s) s (q = e_s) and restart probability c in (0, 1) (Eq. 1).
- * This build supports S == 1. Invalidates scores. */
+/* Set the seed node(s) and the restart probability c in (0, 1) (Eq. 1). Each of
+ * the S seeds (1 <= S <= 256, distinct live ids, host array) gets its own RWR
+ * vector r_j with q = e_{s_j}; seed_idx j of the query calls selects it.
+ * S > 1 keeps the vectors as one n x Sp block (Sp = 32, 64, 128 or 256 columns,
+ * the smallest that holds S) and runs every step as a sparse-matrix times
+ * dense-block product; each column stops on its own test (Algorithm 1's loop
+ * test per seed). Device memory for S > 1: about Sp (16 + 2 b_y) bytes per node
+ * slot (b_y = 8 for FP64, 4 otherwise). A seed cannot be
+ * deleted by a batch. Invalidates scores. */
 osp_status osp_set_seeds(osp_ctx *ctx, const int32_t *seeds, int32_t S, double c);
 
 /* Compute scores from scratch by CPI (Sec. 2.2): x(0) = c e_s, stop after the
- * first x(i) with ||x(i)||_1 <= eps. stats may be NULL. */
+ * first x(i) with ||x(i)||_1 <= eps (per seed when S > 1). stats may be NULL;
+ * with S > 1 its iteration count is the longest seed's and its norms are the
+ * maxima over the seeds (osp_get_seed_stats gives each seed's). */
 osp_status osp_init_scores(osp_ctx *ctx, double eps, osp_batch_stats *stats);
 
 /* Apply one batch of U updates (host array, U <= osp_max_batch()) and update
@@ -210,7 +228,14 @@ osp_status osp_export_graph(osp_ctx *ctx, int direction, int64_t *ptr, int32_t *
 /* Current node count (ids in use, dead ones included) and live edge count. */
 osp_status osp_get_size(osp_ctx *ctx, int64_t *n, int64_t *m);
 
-/* ||x(0)||_1 .. ||x(k)||_1 of the last init/apply call (host, up to cap entries). */
+/* Per seed of the last init/apply call (host arrays of up to cap entries, any of
+ * them NULL to skip): the steps the seed ran, ||x(0)||_1 (its ||q_offset||_1)
+ * and ||x(k)||_1 at its stop. *count = min(S, cap). */
+osp_status osp_get_seed_stats(osp_ctx *ctx, int32_t *iterations, double *qoff_l1,
+                              double *last_l1, int32_t cap, int32_t *count);
+
+/* ||x(0)||_1 .. ||x(k)||_1 of the last init/apply call (host, up to cap entries;
+ * with several seeds each entry is the maximum over the seeds that ran the step). */
 osp_status osp_get_l1_history(osp_ctx *ctx, double *out, int32_t cap, int32_t *count);
 
 /* Device time in microseconds of the parts of the last init/apply propagation

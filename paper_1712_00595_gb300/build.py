@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libosp_gb300.so")
-SOURCES = ["engine.cu", "ingest.cu", "merge.cu", "propagate.cu", "topk.cu", "topk_noalloc.cu"]
+SOURCES = ["engine.cu", "ingest.cu", "merge.cu", "propagate.cu", "topk.cu", "topk_noalloc.cu", "multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

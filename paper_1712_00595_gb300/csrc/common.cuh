@@ -50,6 +50,7 @@ struct Ctl {
   int n_tasks;                 // pull step: warp tasks
   int n_mpieces;               // merge pieces of the current batch
   int dense0;                  // 1: x(0) is found by a dense scan of xacc (no queue from the merge)
+  int n_opieces;               // several seeds: offset items (256 entries of a changed row)
   int epoch;                   // frontier mark of x(0); step i uses epoch + i
   int q_size[2];               // frontier queue lengths
   unsigned int bar_count, bar_gen;
@@ -59,8 +60,27 @@ struct Ctl {
   long long ef;                // out-edges of the current frontier
   long long push_f, push_r;    // sums of |F(i-1)| and |F(i)| over push steps
   int seed;
-  int pad0;
+  int multi;                   // 1: several seeds (the Multi block of Dev), 0: one seed
   double c;
+};
+
+constexpr int kMaxSeeds = 256;
+
+// Several seeds tracked together: column j of each n x Sp block belongs to
+// seed j (Sp = 32 K, K in {1, 2, 4, 8}; columns S .. Sp-1 stay zero). Lane l of
+// a warp owns the K contiguous columns [K l, K l + K) of a row.
+struct Multi {
+  int S, Sp, K;
+  int* seeds;          // [S] internal ids
+  double* r;           // [nc Sp] scores (unnormalised r_temp)
+  double* xacc;        // [nc Sp] offset accumulator
+  void* y0; void* y1;  // [nc Sp] gather vectors (double, float or bf16)
+  double* part;        // [kMaxGrid Sp] per-CTA |x| partials
+  int* active;         // [Sp] 1 while the column still propagates
+  int* col_iters;      // [Sp] steps run per column
+  double* col_q;       // [Sp] ||x(0)||_1 per column
+  double* col_last;    // [Sp] ||x(k)||_1 at the column's stop
+  void* hub_acc;       // [hubs Sp] (float or double) partial sums of long in-lists
 };
 
 // Every device pointer of one engine, passed to kernels by value.
@@ -84,6 +104,7 @@ struct Dev {
   int* mark;           // frontier membership stamps
   int* q0; int* q1;    // frontier queues
   unsigned char* dead;
+  unsigned char* seedflag;  // 1 for the seed node(s): they cannot be deleted
   int* del_pos;        // first deletion position in the batch (kNoPos if none)
   int* rflag; int* cflag;
   // batch scratch: net edits grouped per changed row / column
@@ -108,6 +129,7 @@ struct Dev {
   double* l1_hist;                      // [kMaxHist]
   unsigned long long* step_ns;          // [kMaxHist + 1] device clock at kernel start and after each step
   Ctl* ctl;
+  Multi mu;  // several seeds (unused with one seed)
 };
 
 // Radix-select state of a top-k query.

@@ -38,7 +38,11 @@ struct osp_ctx {
   unsigned long long cap_r = 0, cap_c = 0, top_r = 0, top_c = 0;
   bool loaded = false, seeded = false, scored = false;
   int seed = -1;
+  int S = 1;                   // seeds tracked (S > 1: the seed block d.mu)
   double c = 0.15;
+  int grid_multi = 0;
+  int grid_multi_init = 0;
+  std::vector<void*> mallocs;  // buffers of the seed block, freed when the seeds change
   int fixed_iters = 0;
   int grid_prop = 0;
   int last_iters = 0;
@@ -86,7 +90,8 @@ osp_status cuda_fail(osp_ctx* ctx, cudaError_t e, const char* where) {
   } while (0)
 
 template <typename T>
-osp_status dalloc(osp_ctx* ctx, T** p, size_t count, int fill = 0) {
+osp_status dalloc(osp_ctx* ctx, T** p, size_t count, int fill = 0,
+                  std::vector<void*>* list = nullptr) {
   void* q = nullptr;
   size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
   cudaError_t e = cudaMalloc(&q, bytes);
@@ -96,13 +101,21 @@ osp_status dalloc(osp_ctx* ctx, T** p, size_t count, int fill = 0) {
   }
   e = cudaMemsetAsync(q, fill, bytes, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
-  ctx->allocs.push_back(q);
+  (list ? list : &ctx->allocs)->push_back(q);
   *p = (T*)q;
   return OSP_OK;
 }
 
-void free_all(osp_ctx* ctx) {
+void free_multi(osp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->mallocs) cudaFree(p);
+  ctx->mallocs.clear();
+  ctx->d.mu = Multi{};
+  ctx->S = 1;
+}
+
+void free_all(osp_ctx* ctx) {
+  free_multi(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->d = Dev{};
@@ -345,7 +358,8 @@ osp_status plan_pull(osp_ctx* ctx, int64_t n_bound, int64_t m_bound) {
   return OSP_OK;
 }
 
-osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_bound) {
+osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_bound,
+                           bool init = false) {
   PropParams pp;
   pp.eps = eps;
   pp.max_iter = default_max_iter(ctx, eps);
@@ -357,7 +371,17 @@ osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_
   osp_status s = plan_pull(ctx, n_bound, m_bound);
   if (s != OSP_OK) return s;
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-  CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
+  if (ctx->S > 1) {
+    // bf16 gather vectors carry the small offsets of batches; the initial CPI
+    // (total mass 1) runs with float gather vectors
+    const int prec = init && ctx->opt.precision == OSP_PREC_BF16_ACC64 ? (int)OSP_PREC_FP32_ACC64
+                                                                       : ctx->opt.precision;
+    CK(launch_propagate_multi(ctx->d, pp, prec, prec == ctx->opt.precision ? ctx->grid_multi
+                                                                             : ctx->grid_multi_init,
+                              ctx->stream));
+  }
+  else
+    CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
   ++ctx->launches;
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
   return OSP_OK;
@@ -401,6 +425,12 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
   ++ctx->launches;
   k_merge_write<<<g, 256, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;
+  if (ctx->S > 1) {  // the seed block's offset, from the old and new out-lists
+    k_offset_multi_plan<<<1, 1024, 0, ctx->stream>>>(ctx->d);
+    ++ctx->launches;
+    CK(launch_offset_multi(ctx->d, g, ctx->stream));
+    ++ctx->launches;
+  }
   CK(cudaGetLastError());
   s = run_propagation(ctx, eps, std::min<int64_t>(ctx->n + U, ctx->nc - 1), ctx->m + U);
   if (s != OSP_OK) return s;
@@ -443,7 +473,8 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
   osp_ctx* ctx = new osp_ctx();
   if (opt) ctx->opt = *opt;
   else osp_default_options(&ctx->opt);
-  if (ctx->opt.precision != OSP_PREC_FP64 && ctx->opt.precision != OSP_PREC_FP32_ACC64) {
+  if (ctx->opt.precision != OSP_PREC_FP64 && ctx->opt.precision != OSP_PREC_FP32_ACC64 &&
+      ctx->opt.precision != OSP_PREC_BF16_ACC64) {
     delete ctx;
     return OSP_EINVAL;
   }
@@ -472,7 +503,7 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
     cudaGetLastError();
     return OSP_ECUDA;
   }
-  ctx->grid_prop = propagate_grid(ctx->opt.precision == OSP_PREC_FP32_ACC64, ctx->num_sms);
+  ctx->grid_prop = propagate_grid(ctx->opt.precision != OSP_PREC_FP64, ctx->num_sms);
   if (ctx->grid_prop <= 0) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     cudaFreeHost(ctx->pinned);
@@ -595,6 +626,7 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(d.q0, nc, 0);
   AL(d.q1, nc, 0);
   AL(d.dead, nc, 0);
+  AL(d.seedflag, nc, 0);
   AL(d.del_pos, nc, 0x7F);
   AL(d.rflag, nc, 0);
   AL(d.cflag, nc, 0);
@@ -689,33 +721,92 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
   if (!ctx) return OSP_EINVAL;
   if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
   if (ctx->broken) return fail(ctx, OSP_ESTATE, "context is broken by an earlier device error");
-  if (S != 1) {
-    if (S < 1 || !seeds) return fail(ctx, OSP_EINVAL, "need at least one seed");
-    return fail(ctx, OSP_ENOTSUP, "this build tracks one seed per context");
+  if (!seeds || S < 1 || S > kMaxSeeds)
+    return fail(ctx, OSP_EINVAL, "need between 1 and 256 seeds");
+  if (!(c > 0.0 && c < 1.0)) return fail(ctx, OSP_EINVAL, "c must lie in (0, 1)");
+  std::vector<int32_t> sorted(seeds, seeds + S);
+  std::sort(sorted.begin(), sorted.end());
+  for (int i = 0; i < S; ++i) {
+    if (sorted[i] < 0 || sorted[i] >= ctx->n) return fail(ctx, OSP_EINVAL, "seed id out of range");
+    if (i > 0 && sorted[i] == sorted[i - 1]) return fail(ctx, OSP_EINVAL, "duplicate seed");
   }
-  if (!seeds || !(c > 0.0 && c < 1.0)) return fail(ctx, OSP_EINVAL, "bad seed list or c");
-  if (seeds[0] < 0 || seeds[0] >= ctx->n) return fail(ctx, OSP_EINVAL, "seed id out of range");
+  if (S == 1 && ctx->opt.precision == OSP_PREC_BF16_ACC64)
+    return fail(ctx, OSP_ENOTSUP, "bf16 gather vectors are built for two or more seeds");
   CK(cudaSetDevice(ctx->device));
-  const int32_t s_int = ctx->e2i[seeds[0]];
-  unsigned char dead = 0;
-  CK(cudaMemcpy(&dead, ctx->d.dead + s_int, 1, cudaMemcpyDeviceToHost));
-  if (dead) return fail(ctx, OSP_EINVAL, "seed is a deleted node");
+  std::vector<int32_t> s_int(S);
+  for (int i = 0; i < S; ++i) {
+    s_int[i] = ctx->e2i[seeds[i]];
+    unsigned char dead = 0;
+    CK(cudaMemcpy(&dead, ctx->d.dead + s_int[i], 1, cudaMemcpyDeviceToHost));
+    if (dead) return fail(ctx, OSP_EINVAL, "seed is a deleted node");
+  }
+  free_multi(ctx);
+  ctx->seeded = ctx->scored = false;
   Ctl h;
   osp_status s = read_ctl(ctx, &h);
   if (s != OSP_OK) return s;
-  h.seed = s_int;
+  h.seed = s_int[0];
   h.c = c;
+  h.multi = S > 1;
   s = write_ctl(ctx, h);
   if (s != OSP_OK) return s;
   ctx->seed = seeds[0];
   ctx->c = c;
+  CK(cudaMemsetAsync(ctx->d.seedflag, 0, ctx->nc, ctx->stream));
+  for (int i = 0; i < S; ++i) CK(cudaMemsetAsync(ctx->d.seedflag + s_int[i], 1, 1, ctx->stream));
   k_set_scale<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->d, (int)ctx->n, c);
   ++ctx->launches;
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
+  if (S > 1) {
+    // the seed block: n x Sp per vector, Sp = 32 K with K in {1, 2, 4, 8}
+    Multi& M = ctx->d.mu;
+    const int K = S <= 32 ? 1 : S <= 64 ? 2 : S <= 128 ? 4 : 8;
+    const size_t cells = (size_t)ctx->nc * 32 * K;
+    // bf16 batches keep float-sized gather blocks: the initial CPI runs in float
+    const size_t ybytes = ctx->opt.precision == OSP_PREC_FP64 ? 8 : 4;
+    const size_t nh = (size_t)(ctx->cap_c / kHubThreshold) + 2;
+    unsigned char* y0 = nullptr;
+    unsigned char* y1 = nullptr;
+    double* hub = nullptr;
+#define ML(p, cnt)                                                    \
+  do {                                                                \
+    s = dalloc(ctx, &(p), (size_t)(cnt), 0, &ctx->mallocs);           \
+    if (s != OSP_OK) {                                                \
+      free_multi(ctx);                                                \
+      return s;                                                       \
+    }                                                                 \
+  } while (0)
+    ML(M.seeds, S);
+    ML(M.r, cells);
+    ML(M.xacc, cells);
+    ML(y0, cells * ybytes);
+    ML(y1, cells * ybytes);
+    ML(M.part, (size_t)kMaxGrid * 32 * K);
+    ML(M.active, 32 * K);
+    ML(M.col_iters, 32 * K);
+    ML(M.col_q, 32 * K);
+    ML(M.col_last, 32 * K);
+    ML(hub, nh * 32 * K);
+#undef ML
+    M.S = S;
+    M.K = K;
+    M.Sp = 32 * K;
+    M.y0 = y0;
+    M.y1 = y1;
+    M.hub_acc = hub;
+    CK(cudaMemcpyAsync(M.seeds, s_int.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->grid_multi = propagate_multi_grid(ctx->opt.precision, K, ctx->num_sms);
+    ctx->grid_multi_init = propagate_multi_grid(
+        ctx->opt.precision == OSP_PREC_FP64 ? OSP_PREC_FP64 : OSP_PREC_FP32_ACC64, K, ctx->num_sms);
+    if (ctx->grid_multi <= 0 || ctx->grid_multi_init <= 0) {
+      free_multi(ctx);
+      return fail(ctx, OSP_ECUDA, "no resident grid for the seed-block kernel");
+    }
+    ctx->S = S;
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->seeded = true;
-  ctx->scored = false;
   ctx->err.clear();
   return OSP_OK;
 }
@@ -726,13 +817,19 @@ osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
   if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
   ctx->launches = 0;
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-  CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
   k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;
-  k_cpi_begin<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  if (ctx->S > 1) {
+    const Multi& M = ctx->d.mu;
+    CK(cudaMemsetAsync(M.r, 0, sizeof(double) * (size_t)ctx->nc * M.Sp, ctx->stream));
+    k_multi_cpi_begin<<<1, kMaxSeeds, 0, ctx->stream>>>(ctx->d);
+  } else {
+    CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
+    k_cpi_begin<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  }
   ++ctx->launches;
   CK(cudaGetLastError());
-  s = run_propagation(ctx, eps, ctx->n, ctx->m);
+  s = run_propagation(ctx, eps, ctx->n, ctx->m, true);
   if (s != OSP_OK) return s;
   s = finish_call(ctx, ctx->m, stats);
   if (s == OSP_OK || s == OSP_ENOCONV) ctx->scored = true;
@@ -762,11 +859,15 @@ osp_status osp_apply_updates(osp_ctx* ctx, const osp_update* ops, int64_t U, dou
   return apply_common(ctx, ctx->ops_stage, U, eps, stats);
 }
 
-// Scores in caller order into dst (device), optionally divided by ||r||_1.
-osp_status scores_in_caller_order(osp_ctx* ctx, int normalize, double* dst) {
+// Scores of seed column col in caller order into dst (device), optionally
+// divided by their L1 norm.
+osp_status scores_in_caller_order(osp_ctx* ctx, int col, int normalize, double* dst) {
   const int n = (int)ctx->n;
   cudaStream_t st = ctx->stream;
-  k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dst);
+  if (ctx->S > 1)
+    k_gather_col<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.mu.r, ctx->d.mu.Sp, col, ctx->d.ext2int, n, dst);
+  else
+    k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dst);
   if (normalize) {
     CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), st));
     k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(dst, n, ctx->dsum);
@@ -779,8 +880,9 @@ osp_status scores_in_caller_order(osp_ctx* ctx, int normalize, double* dst) {
 osp_status osp_query_device(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out_device) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
-  if (seed_idx != 0 || !out_device) return fail(ctx, OSP_EINVAL, "bad seed index or output");
-  s = scores_in_caller_order(ctx, normalize, out_device);
+  if (seed_idx < 0 || seed_idx >= ctx->S || !out_device)
+    return fail(ctx, OSP_EINVAL, "bad seed index or output");
+  s = scores_in_caller_order(ctx, seed_idx, normalize, out_device);
   if (s != OSP_OK) return s;
   CK(cudaStreamSynchronize(ctx->stream));
   return OSP_OK;
@@ -789,8 +891,9 @@ osp_status osp_query_device(osp_ctx* ctx, int32_t seed_idx, int normalize, doubl
 osp_status osp_query(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
-  if (seed_idx != 0 || !out) return fail(ctx, OSP_EINVAL, "bad seed index or output");
-  s = scores_in_caller_order(ctx, normalize, ctx->dtmp);
+  if (seed_idx < 0 || seed_idx >= ctx->S || !out)
+    return fail(ctx, OSP_EINVAL, "bad seed index or output");
+  s = scores_in_caller_order(ctx, seed_idx, normalize, ctx->dtmp);
   if (s != OSP_OK) return s;
   CK(cudaMemcpyAsync(out, ctx->dtmp, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -801,13 +904,13 @@ osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, in
                     double* scores, int32_t* k_out) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
-  if (seed_idx != 0 || k <= 0 || k > kTopkMaxK || !ids || !scores || !k_out)
+  if (seed_idx < 0 || seed_idx >= ctx->S || k <= 0 || k > kTopkMaxK || !ids || !scores || !k_out)
     return fail(ctx, OSP_EINVAL, "bad seed index, k outside [1, 4096] or null output");
   const int n = (int)ctx->n;
   const int g = ctx->num_sms * 4;
   cudaStream_t st = ctx->stream;
   // rank the scores in caller order, so that ties go to the smaller caller id
-  s = scores_in_caller_order(ctx, 0, ctx->dtmp);
+  s = scores_in_caller_order(ctx, seed_idx, 0, ctx->dtmp);
   if (s != OSP_OK) return s;
   const double* rs = ctx->dtmp;
   k_topk_reset<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, k);
@@ -896,6 +999,31 @@ osp_status osp_get_step_times(osp_ctx* ctx, double* us, int32_t cap, int32_t* co
   std::vector<unsigned long long> t(k + 1);
   CK(cudaMemcpy(t.data(), ctx->d.step_ns, sizeof(unsigned long long) * (k + 1), cudaMemcpyDeviceToHost));
   for (int i = 0; i < k; ++i) us[i] = (double)(t[i + 1] - t[i]) * 1e-3;
+  *count = k;
+  return OSP_OK;
+}
+
+osp_status osp_get_seed_stats(osp_ctx* ctx, int32_t* iterations, double* qoff_l1,
+                              double* last_l1, int32_t cap, int32_t* count) {
+  if (!ctx || !count || cap < 0) return OSP_EINVAL;
+  if (!ctx->seeded) return fail(ctx, OSP_ESTATE, "no seed set");
+  CK(cudaSetDevice(ctx->device));
+  const int k = std::min<int>(ctx->S, cap);
+  cudaStream_t st = ctx->stream;
+  if (ctx->S > 1) {
+    const Multi& M = ctx->d.mu;
+    if (iterations && k)
+      CK(cudaMemcpyAsync(iterations, M.col_iters, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st));
+    if (qoff_l1 && k) CK(cudaMemcpyAsync(qoff_l1, M.col_q, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    if (last_l1 && k) CK(cudaMemcpyAsync(last_l1, M.col_last, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  } else if (k > 0) {
+    if (iterations) iterations[0] = ctx->last_iters;
+    const int last = std::min(ctx->last_iters, kMaxHist - 1);
+    if (qoff_l1) CK(cudaMemcpyAsync(qoff_l1, ctx->d.l1_hist, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (last_l1)
+      CK(cudaMemcpyAsync(last_l1, ctx->d.l1_hist + last, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
   *count = k;
   return OSP_OK;
 }

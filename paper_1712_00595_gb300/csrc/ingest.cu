@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   Ctl* ctl = d.ctl;
   const int tid = threadIdx.x;
   const int n_old = ctl->n;
-  const int seed = ctl->seed;
   if (tid == 0) {
     s_bad = kNoPos;
     s_ndel = 0;
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
     } else if (o.op == OSP_OP_DELETE_NODE) {
       const int na = n_old + run;
       const int w = o.u;
-      if (w >= 0 && w < na && !d.dead[w] && w != seed) atomicMin(&d.del_pos[w], p);
+      if (w >= 0 && w < na && !d.dead[w] && !d.seedflag[w]) atomicMin(&d.del_pos[w], p);
       else atomicMin(&s_bad, p);
     }
   }
@@ -237,7 +236,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       ok = true;
       ++run;
     } else if (o.op == OSP_OP_DELETE_NODE) {
-      ok = o.u >= 0 && o.u < na && !d.dead[o.u] && o.u != seed && d.del_pos[o.u] == p;
+      ok = o.u >= 0 && o.u < na && !d.dead[o.u] && !d.seedflag[o.u] && d.del_pos[o.u] == p;
     } else {
       ok = false;
     }

@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
   const double c1 = 1.0 - ctl->c;
   const int epoch = ctl->epoch;
   const bool queue = !ctl->dense0;
+  const bool multi = ctl->multi;
   const bool any_dead = ctl->n_del > 0;  // only nodes deleted by this batch still have edges
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
     const unsigned o = d.rec_old_off[c];
     const int L = d.rec_old_len[c];
     const bool cleared = any_dead && d.dead[R.node];
-    const double ru = R.rows ? d.r[R.node] : 0.0;
+    const double ru = R.rows && !multi ? d.r[R.node] : 0.0;  // the seed block has its own offset kernel
     const bool contrib = R.rows && ru != 0.0;
     const double wa = L ? 1.0 / (double)L : 0.0;
     int cnt = 0;
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
   const double c1 = 1.0 - ctl->c;
   const int epoch = ctl->epoch;
   const bool queue = !ctl->dense0;
+  const bool multi = ctl->multi;
   const bool any_dead = ctl->n_del > 0;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
     const int* I = R.ins + R.is;
     const int ic = R.ic;
     const bool cleared = any_dead && d.dead[R.node];
-    const double ru = R.rows ? d.r[R.node] : 0.0;
+    const double ru = R.rows && !multi ? d.r[R.node] : 0.0;  // the seed block has its own offset kernel
     const bool contrib = R.rows && ru != 0.0;
     const double wa = L ? 1.0 / (double)L : 0.0;
     const double wb = dp ? 1.0 / (double)dp : 0.0;

@@ -1,0 +1,500 @@
+// Several seeds at once: the columns of an n x Sp block (Sp = 32 K) each hold
+// the RWR vector of one seed, so every step of Algorithm 1 becomes a sparse
+// matrix times a dense block (SpMM) and every gathered source brings K
+// contiguous values per lane instead of one.
+//
+//   offset   q_offset = (1-c)(B~^T - A~^T) R_old over the changed rows u
+//            (Sec. 3.1, 3.3): row u adds (1-c) R_old[u] / d'_u to every entry
+//            of its new out-list and subtracts (1-c) R_old[u] / d_u from every
+//            entry of its old out-list (old lists stay readable: the merge
+//            writes new lists out of place). Targets get this call's stamp.
+//   x(0)     one pass over all nodes: stamped rows move from xacc into R and
+//            the first gather block y(0) = x(0) (1-c) / d; other rows of y(0)
+//            are written as zero.
+//   steps    pull only: x(i)[v] = sum over the in-list of v of y(i-1)[u],
+//            a warp per node, lanes over columns; long in-lists in pieces.
+//   stop     per column (Algorithm 1 loop test, do-while form): a column whose
+//            ||x(i)||_1 <= eps stops adding and propagating; the call ends
+//            when no column is left or at the iteration cap.
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "gridbar.cuh"
+#include "kernels.h"
+
+namespace osp {
+namespace {
+
+template <typename TY> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ __nv_bfloat16 from_acc(float v, __nv_bfloat16*) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from_acc(float v, float*) { return v; }
+__device__ __forceinline__ double from_acc(double v, double*) { return v; }
+
+// K contiguous elements (K * sizeof(T) bytes, naturally aligned) through L2.
+template <typename T, int K>
+__device__ __forceinline__ void load_cg(const T* p, T (&out)[K]) {
+  constexpr int B = K * (int)sizeof(T);
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i)
+      reinterpret_cast<uint4*>(out)[i] = __ldcg(reinterpret_cast<const uint4*>(p) + i);
+  } else if constexpr (B == 8) {
+    *reinterpret_cast<uint2*>(out) = __ldcg(reinterpret_cast<const uint2*>(p));
+  } else if constexpr (B == 4) {
+    *reinterpret_cast<unsigned*>(out) = __ldcg(reinterpret_cast<const unsigned*>(p));
+  } else {
+    *reinterpret_cast<unsigned short*>(out) = __ldcg(reinterpret_cast<const unsigned short*>(p));
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void store_k(T* p, const T (&v)[K]) {
+  constexpr int B = K * (int)sizeof(T);
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i)
+      reinterpret_cast<uint4*>(p)[i] = reinterpret_cast<const uint4*>(v)[i];
+  } else if constexpr (B == 8) {
+    *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(v);
+  } else if constexpr (B == 4) {
+    *reinterpret_cast<unsigned*>(p) = *reinterpret_cast<const unsigned*>(v);
+  } else {
+    *reinterpret_cast<unsigned short*>(p) = *reinterpret_cast<const unsigned short*>(v);
+  }
+}
+
+// Per-column |x| partials of this CTA: lanes hold their K columns; warps are
+// combined in shared memory in a fixed order.
+template <int K>
+__device__ __forceinline__ void column_partials(const Multi& M, const double (&l1)[K],
+                                                double* s_part) {
+  constexpr int Sp = 32 * K;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) s_part[w * Sp + lane * K + k] = l1[k];
+  __syncthreads();
+  for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < kPropWarps; ++i) a += s_part[i * Sp + j];
+    M.part[(size_t)blockIdx.x * Sp + j] = a;
+  }
+  __threadfence();
+}
+
+// Whole last CTA: per-column sums of the partials (fixed order over CTAs),
+// per-column stopping, the call's stop and the history entry (max over the
+// columns that ran the step).
+template <int K>
+__device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long long m) {
+  constexpr int Sp = 32 * K;
+  const Multi& M = d.mu;
+  Ctl* ctl = d.ctl;
+  __shared__ double s_max[kPropThreads / 32];
+  double seen = 0.0;
+  int live = 0;
+  for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
+    double L = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) L += __ldcg(M.part + (size_t)b * Sp + j);
+    if (j >= M.S) continue;
+    if (it == 0) {
+      M.col_q[j] = L;
+      M.col_last[j] = L;
+      M.col_iters[j] = 0;
+      M.active[j] = 1;
+      seen = fmax(seen, L);
+      live = 1;
+    } else if (*(volatile int*)&M.active[j]) {
+      M.col_iters[j] = it;
+      M.col_last[j] = L;
+      seen = fmax(seen, L);
+      int stop = pp.force_iters > 0 ? it >= pp.force_iters : L <= pp.eps;
+      if (!stop && it >= pp.max_iter) {
+        stop = 1;
+        ctl->noconv = 1;
+      }
+      if (stop) M.active[j] = 0;
+      else live = 1;
+    }
+  }
+  seen = warp_max(seen);
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = seen;
+  const int any = __syncthreads_or(live);
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < kPropWarps; ++i) mx = fmax(mx, s_max[i]);
+    if (it < kMaxHist) {
+      d.l1_hist[it] = mx;
+      d.step_ns[it + 1] = global_ns();
+    }
+    ctl->iter = it;
+    if (it > 0) {
+      ctl->visited += m;
+      ctl->pull_used = 1;
+    }
+    ctl->stop = !any;
+    for (int i = 0; i < 4; ++i) ctl->ctr[i] = 0;
+  }
+}
+
+// x(i)[v] from the K-column sums acc: add into R for running columns, write
+// the next gather row (zero for stopped columns), accumulate |x|.
+template <typename TY, int K, typename A>
+__device__ __forceinline__ void finish_row(const Dev& d, int v, const A (&acc)[K], unsigned act,
+                                           TY* yd, double (&l1)[K]) {
+  constexpr int Sp = 32 * K;
+  const int lane = threadIdx.x & 31;
+  const size_t base = (size_t)v * Sp + lane * K;
+  const A s = std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
+  alignas(16) double rr[K];
+  load_cg(d.mu.r + base, rr);
+  alignas(16) TY yv[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (act & (1u << k)) {
+      const double x = (double)acc[k];
+      rr[k] += x;
+      l1[k] += fabs(x);
+      yv[k] = from_acc((A)(acc[k] * s), (TY*)nullptr);
+    } else {
+      yv[k] = from_acc((A)0, (TY*)nullptr);
+    }
+  }
+  store_k(d.mu.r + base, rr);
+  store_k(yd + base, yv);
+}
+
+// Sum of y rows over in-list entries p[0 .. len), four rows in flight.
+template <typename TY, int K, typename A>
+__device__ __forceinline__ void sum_rows(const int* p, int len, const TY* ys, A (&acc)[K]) {
+  constexpr int Sp = 32 * K;
+  const int lane = threadIdx.x & 31;
+  for (int b = 0; b < len; b += 32) {
+    const int cnt = min(32, len - b);
+    const int idx = lane < cnt ? __ldg(p + b + lane) : 0;
+    int j = 0;
+    for (; j + 4 <= cnt; j += 4) {
+      const int u0 = __shfl_sync(0xffffffffu, idx, j);
+      const int u1 = __shfl_sync(0xffffffffu, idx, j + 1);
+      const int u2 = __shfl_sync(0xffffffffu, idx, j + 2);
+      const int u3 = __shfl_sync(0xffffffffu, idx, j + 3);
+      alignas(16) TY a0[K], a1[K], a2[K], a3[K];
+      load_cg(ys + (size_t)u0 * Sp + lane * K, a0);
+      load_cg(ys + (size_t)u1 * Sp + lane * K, a1);
+      load_cg(ys + (size_t)u2 * Sp + lane * K, a2);
+      load_cg(ys + (size_t)u3 * Sp + lane * K, a3);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        acc[k] += (to_acc(a0[k]) + to_acc(a1[k])) + (to_acc(a2[k]) + to_acc(a3[k]));
+    }
+    for (; j < cnt; ++j) {
+      const int u = __shfl_sync(0xffffffffu, idx, j);
+      alignas(16) TY a[K];
+      load_cg(ys + (size_t)u * Sp + lane * K, a);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += to_acc(a[k]);
+    }
+  }
+}
+
+}  // namespace
+
+// One CTA: offset items of the changed rows (256 entries of old + new list each).
+__global__ void __launch_bounds__(1024) k_offset_multi_plan(Dev d) {
+  __shared__ int s_w[32];
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int nr = ctl->n_rec_r;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (nr + 1023) / 1024;
+  const int lo = min(nr, tid * per), hi = min(nr, lo + per);
+  int mine = 0;
+  for (int c = lo; c < hi; ++c) mine += (d.rec_old_len[c] + d.rec_dp[c] + kPiece - 1) / kPiece;
+  int x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = s_w[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    s_w[lane] = t;
+  }
+  __syncthreads();
+  int base = (w ? s_w[w - 1] : 0) + x - mine;
+  for (int c = lo; c < hi; ++c) {
+    const int np = (d.rec_old_len[c] + d.rec_dp[c] + kPiece - 1) / kPiece;
+    d.rec_pstart[c] = base;
+    for (int q = 0; q < np; ++q) d.piece_rec[base + q] = c;
+    base += np;
+  }
+  if (tid == 0) ctl->n_opieces = s_w[31];
+}
+
+// Warp per offset item: R_old[u] times -(1-c)/d_u into xacc over the old
+// out-list entries, times +(1-c)/d'_u over the new ones; stamps the targets.
+template <int K>
+__global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
+  constexpr int Sp = 32 * K;
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const int np = ctl->n_opieces;
+  const double c1 = 1.0 - ctl->c;
+  const int epoch = ctl->epoch;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = gw; p < np; p += nw) {
+    const int c = d.piece_rec[p];
+    const int q = p - d.rec_pstart[c];
+    const int u = d.rec_r_node[c];
+    const int L = d.rec_old_len[c], dp = d.rec_dp[c];
+    alignas(16) double ru[K];
+    load_cg(d.mu.r + (size_t)u * Sp + lane * K, ru);
+    bool nz = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) nz |= ru[k] != 0.0;
+    if (!__any_sync(0xffffffffu, nz)) continue;
+    const double wa = L ? c1 / (double)L : 0.0;
+    const double wb = dp ? c1 / (double)dp : 0.0;
+    const int* oldl = d.pool_r + d.rec_old_off[c];
+    const int* newl = d.pool_r + d.rec_fbase[c];
+    const int e0 = q * kPiece, e1 = min(e0 + kPiece, L + dp);
+    for (int eb = e0; eb < e1; eb += 32) {
+      const int e = eb + lane;
+      int a = 0;
+      double wgt = 0.0;
+      if (e < e1) {
+        if (e < L) {
+          a = oldl[e];
+          wgt = -wa;
+        } else {
+          a = newl[e - L];
+          wgt = wb;
+        }
+      }
+      if (!OSP_GUARD(ctl, a >= 0 && a < d.nc, "multi offset target", c, e, a)) a = 0;
+      const int cnt = min(32, e1 - eb);
+      for (int j = 0; j < cnt; ++j) {
+        const int aj = __shfl_sync(0xffffffffu, a, j);
+        const double wj = __shfl_sync(0xffffffffu, wgt, j);
+        double* row = d.mu.xacc + (size_t)aj * Sp + lane * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (ru[k] != 0.0) atomicAdd(row + k, wj * ru[k]);
+        if (lane == 0) d.mark[aj] = epoch;
+      }
+    }
+  }
+}
+
+// CPI start for every column: x(0) = c e_{s_j} in column j.
+__global__ void k_multi_cpi_begin(Dev d) {
+  const Multi& M = d.mu;
+  const int j = threadIdx.x;
+  if (j < M.S) {
+    const int s = M.seeds[j];
+    M.xacc[(size_t)s * M.Sp + j] = d.ctl->c;
+    d.mark[s] = d.ctl->epoch;
+  }
+}
+
+// Column col of R in caller order.
+__global__ void k_gather_col(const double* __restrict__ r, int Sp, int col,
+                             const int* __restrict__ ext2int, int n, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = r[(size_t)ext2int[i] * Sp + col];
+}
+
+template <typename TY, int K>
+__global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, PropParams pp) {
+  using A = typename AccOf<TY>::type;
+  constexpr int Sp = 32 * K;
+  __shared__ BarShared sh;
+  __shared__ double s_part[kPropWarps * Sp];
+  Ctl* ctl = d.ctl;
+  if (*(volatile int*)&ctl->status) return;
+  const Multi& M = d.mu;
+  const int n = ctl->n;
+  const long long m = ctl->m;
+  const int epoch = ctl->epoch;
+  const int n_hubs = ctl->n_hubs;
+  const int n_pieces = ctl->n_pieces;
+  const int n_tasks = ctl->n_tasks;
+  TY* yb[2] = {(TY*)M.y0, (TY*)M.y1};
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.step_ns[0] = global_ns();
+
+  // x(0): stamped rows from xacc into R and y(0); other rows of y(0) are zero
+  {
+    double l1[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) l1[k] = 0.0;
+    for (int v = gw; v < n; v += nw) {
+      const size_t base = (size_t)v * Sp + lane * K;
+      alignas(16) TY yv[K];
+      if (__ldcg(d.mark + v) == epoch) {
+        alignas(16) double x[K], rr[K], z[K];
+        load_cg(M.xacc + base, x);
+        load_cg(M.r + base, rr);
+        const A s = std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          rr[k] += x[k];
+          l1[k] += fabs(x[k]);
+          yv[k] = from_acc((A)((A)x[k] * s), (TY*)nullptr);
+          z[k] = 0.0;
+        }
+        store_k(M.r + base, rr);
+        store_k(M.xacc + base, z);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) yv[k] = from_acc((A)0, (TY*)nullptr);
+      }
+      store_k(yb[0] + base, yv);
+    }
+    column_partials<K>(M, l1, s_part);
+    if (bar_arrive(ctl, sh)) decide_multi<K>(d, pp, 0, m);
+    if (!bar_release(ctl, sh)) return;
+  }
+
+  A* hub_acc = (A*)M.hub_acc;
+  for (int it = 1;; ++it) {
+    if (*(volatile int*)&ctl->stop) break;
+    unsigned act = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) act |= (unsigned)(*(volatile int*)&M.active[lane * K + k] != 0) << k;
+    const TY* ys = yb[(it - 1) & 1];
+    TY* yd = yb[it & 1];
+    double l1[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) l1[k] = 0.0;
+    const int n_items = n_pieces + n_tasks;
+    for (;;) {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(&ctl->ctr[1], 1);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= n_items) break;
+      if (t < n_pieces) {
+        // a piece of a long in-list; the piece that completes the list finishes it
+        int lo = 0, hi = n_hubs;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(d.hub_pstart + mid) <= t) lo = mid;
+          else hi = mid;
+        }
+        const int h = lo;
+        const int v = __ldg(d.hubs + h);
+        const int piece = t - __ldg(d.hub_pstart + h);
+        const int full = __ldg(d.len_c + v);
+        const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
+        const int L = min(kHubPiece, full - piece * kHubPiece);
+        A acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = (A)0;
+        sum_rows<TY, K, A>(p, L, ys, acc);
+        A* ha = hub_acc + (size_t)h * Sp + lane * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) atomicAdd(ha + k, acc[k]);
+        __threadfence();
+        int last = 0;
+        if (lane == 0) {
+          const int np = (full + kHubPiece - 1) / kHubPiece;
+          last = atomicAdd(&d.hub_cnt[h], 1) == np - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+          __threadfence();
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            acc[k] = __ldcg(ha + k);
+            ha[k] = (A)0;
+          }
+          if (lane == 0) d.hub_cnt[h] = 0;
+          finish_row<TY, K, A>(d, v, acc, act, yd, l1);
+        }
+        continue;
+      }
+      const int task = t - n_pieces;
+      const int c0 = __ldg(d.task_first + task), c1 = __ldg(d.task_first + task + 1);
+      for (int v = c0; v < c1; ++v) {
+        const int len = __ldg(d.len_c + v);
+        if (len > kHubThreshold) continue;  // summed in pieces
+        A acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = (A)0;
+        sum_rows<TY, K, A>(d.pool_c + __ldg(d.off_c + v), len, ys, acc);
+        finish_row<TY, K, A>(d, v, acc, act, yd, l1);
+      }
+    }
+    column_partials<K>(M, l1, s_part);
+    if (bar_arrive(ctl, sh)) decide_multi<K>(d, pp, it, m);
+    if (!bar_release(ctl, sh)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->epoch = epoch + 1;
+}
+
+namespace {
+
+template <typename TY>
+const void* multi_fn(int K) {
+  switch (K) {
+    case 1: return (const void*)k_propagate_multi<TY, 1>;
+    case 2: return (const void*)k_propagate_multi<TY, 2>;
+    case 4: return (const void*)k_propagate_multi<TY, 4>;
+    default: return (const void*)k_propagate_multi<TY, 8>;
+  }
+}
+
+const void* pick_multi(int precision, int K) {
+  if (precision == OSP_PREC_FP64) return multi_fn<double>(K);
+  if (precision == OSP_PREC_FP32_ACC64) return multi_fn<float>(K);
+  return multi_fn<__nv_bfloat16>(K);
+}
+
+}  // namespace
+
+int propagate_multi_grid(int precision, int K, int num_sms) {
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pick_multi(precision, K), kPropThreads, 0) !=
+          cudaSuccess ||
+      bps <= 0)
+    return 0;
+  bps = bps > 4 ? 4 : bps;
+  const int g = bps * num_sms;
+  return g > kMaxGrid ? kMaxGrid : g;
+}
+
+cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int grid,
+                                   cudaStream_t s) {
+  Dev dd = d;
+  PropParams p = pp;
+  void* args[] = {&dd, &p};
+  return cudaLaunchCooperativeKernel(pick_multi(precision, d.mu.K), dim3(grid), dim3(kPropThreads),
+                                     args, 0, s);
+}
+
+cudaError_t launch_offset_multi(const Dev& d, int grid, cudaStream_t s) {
+  switch (d.mu.K) {
+    case 1: k_offset_multi<1><<<grid, 256, 0, s>>>(d); break;
+    case 2: k_offset_multi<2><<<grid, 256, 0, s>>>(d); break;
+    case 4: k_offset_multi<4><<<grid, 256, 0, s>>>(d); break;
+    default: k_offset_multi<8><<<grid, 256, 0, s>>>(d); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace osp

@@ -10,9 +10,9 @@
 //         next frontier); an epilogue over the new frontier adds x(i) into r,
 //         forms y(i) and sums |x(i)|.
 //   pull: x(i) is dense. Each node v sums y(i-1) over its in-list and the
-//         same pass adds x(i) into r, writes y(i) and sums |x(i)|. CTAs own
-//         node ranges of equal work (edges + nodes); long lists are summed in
-//         pieces by all warps.
+//         same pass adds x(i) into r, writes y(i) and sums |x(i)|. Warps take
+//         tasks of consecutive nodes (about equal edges + nodes) from a
+//         shared counter; long lists are summed in pieces by all warps.
 // The step switches to pull once the frontier's out-edges exceed m / alpha or
 // its size exceeds n / beta, and stays there. Between steps a grid barrier
 // (bounded wait) reduces the per-CTA |x| partials in a fixed order and takes
@@ -21,64 +21,11 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "gridbar.cuh"
 #include "kernels.h"
 
 namespace osp {
 namespace {
-
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
-constexpr unsigned kBarrierMaxSpins = 1u << 26;
-
-struct BarShared {
-  unsigned gen;
-  int last;
-  int ok;
-};
-
-__device__ __forceinline__ bool bar_arrive(Ctl* ctl, BarShared& sh) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g = *(volatile unsigned*)&ctl->bar_gen;
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-    sh.gen = g;
-    sh.last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  return sh.last;
-}
-
-// The last CTA opens the barrier; the others wait with a time limit. Returns
-// false when the kernel must stop (timeout or an error status).
-__device__ __forceinline__ bool bar_release(Ctl* ctl, BarShared& sh) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (sh.last) {
-      ctl->bar_count = 0;
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      unsigned spins = 0;
-      while (*(volatile unsigned*)&ctl->bar_gen == sh.gen) {
-        __nanosleep(32);
-        ++spins;
-        if (spins >= kBarrierMaxSpins ||
-            ((spins & 1023u) == 0 && global_ns() - t0 > kBarrierTimeoutNs)) {
-          atomicCAS(&ctl->status, 0, (int)OSP_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    if (*(volatile int*)&ctl->status != 0) ok = 0;
-    sh.ok = ok;
-  }
-  __syncthreads();
-  return sh.ok;
-}
 
 __device__ __forceinline__ void block_partials(const Dev& d, double l1, long long ef, double* s_l1,
                                                long long* s_ef) {

@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("OSP_LIBRARY") or os.path.join(HERE, "_build", "libosp
 
 OSP_OK, OSP_EINVAL, OSP_ENOMEM, OSP_ECUDA, OSP_ETIMEOUT, OSP_ENOCONV, OSP_ESTATE, OSP_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6, -7)
-OSP_PREC_FP64, OSP_PREC_FP32_ACC64 = 0, 1
+OSP_PREC_FP64, OSP_PREC_FP32_ACC64, OSP_PREC_BF16_ACC64 = 0, 1, 2
 UPDATE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("op", "<i4")])
 
 TOPK_NOALLOC_MAX_N = 16777216  # OSP_TOPK_NOALLOC_MAX_N
@@ -29,7 +29,7 @@ EXPORTED = [
     "osp_init_scores", "osp_apply_updates", "osp_apply_updates_device", "osp_max_batch",
     "osp_query", "osp_query_device", "osp_topk", "osp_export_graph", "osp_get_size",
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
-    "osp_status_string", "osp_topk_noalloc",
+    "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
 ]
 
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
             "osp_last_error": (C.c_char_p, [P]),
             "osp_status_string": (C.c_char_p, [C.c_int]),
             "osp_topk_noalloc": (C.c_int, [P, i64, i32, C.c_int, P, P, P, P]),
+            "osp_get_seed_stats": (C.c_int, [P, P, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -241,6 +242,17 @@ class Engine:
         cnt = C.c_int32(0)
         self._check(self._L.osp_get_l1_history(self._h, _ptr(out), int(cap), C.byref(cnt)))
         return out[: cnt.value]
+
+    def get_seed_stats(self, cap=256):
+        """Per seed of the last call: (steps run, ||x(0)||_1, ||x(k)||_1 at its stop)."""
+        it = np.empty(cap, np.int32)
+        q = np.empty(cap, np.float64)
+        last = np.empty(cap, np.float64)
+        cnt = C.c_int32(0)
+        self._check(self._L.osp_get_seed_stats(self._h, _ptr(it), _ptr(q), _ptr(last), int(cap),
+                                               C.byref(cnt)))
+        k = cnt.value
+        return it[:k], q[:k], last[:k]
 
     def get_step_times(self, cap=4096):
         """Microseconds of the x(0) pass and of each propagation step of the last call."""
