@@ -43,6 +43,22 @@ HUB_SEED_OFFSET = 2
 STREAM_SEED_OFFSET = 202
 
 
+# Several seeds at once (the n x Sp seed block). Sizes at full scale.
+MULTI_WORKLOADS = {
+    # undirected Chung-Lu (exponent 2.1, mean degree 16): 4,194,304 nodes,
+    # 33,554,432 undirected edges stored in both directions; 64 uniform seeds;
+    # batches of log-uniform 10 .. 8,192 undirected edges (each = 2 directed ops,
+    # half insertions, half deletions); FP32 gather vectors, FP64 sums
+    "chunglu22_s64": {"graph": "chunglu", "log2n": 22, "m": 33554432, "S": 64,
+                      "precision": "fp32", "eps": 1e-6, "batches": 50},
+    # directed R-MAT scale 24: 16,777,216 nodes, 268,435,456 edges; 256 uniform
+    # seeds; batches of 10,000 ops: 500 edge ops, 1,000 new nodes with 8
+    # out-edges each, 500 node deletions; bf16 gather vectors, FP64 sums
+    "rmat24_s256": {"graph": "rmat", "log2n": 24, "m": 268435456, "S": 256,
+                    "precision": "bf16", "eps": 1e-6, "batches": 20},
+}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -55,6 +71,12 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU time bound of the cpu_baseline sample (whole batches)")
+    p.add_argument("--workload", default="rmat20", choices=["rmat20"] + sorted(MULTI_WORKLOADS),
+                   help="rmat20: the one-seed headline; the others track many seeds at once")
+    p.add_argument("--log2n", type=int, default=0,
+                   help="several-seed workloads: nodes 2^log2n (edges scaled alike; 0 = full size)")
+    p.add_argument("--fp64-seeds", type=int, default=8,
+                   help="several-seed workloads: seeds compared with the FP64 replay (0 = skip)")
     return p.parse_args()
 
 
@@ -422,11 +444,155 @@ def run_ours(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+def make_multi_workload(name, log2n):
+    cfg = MULTI_WORKLOADS[name]
+    full = cfg["log2n"]
+    log2n = log2n or full
+    n = 1 << log2n
+    m = cfg["m"] >> (full - log2n) if log2n <= full else cfg["m"] << (log2n - full)
+    S, batches = cfg["S"], cfg["batches"]
+    base = W.BASE_SEED + (3 if cfg["graph"] == "chunglu" else 5)
+    if cfg["graph"] == "chunglu":
+        gen, lo, hi = W.chung_lu_graph(n, m, seed=base)
+        src = np.concatenate([lo, hi])
+        dst = np.concatenate([hi, lo])
+        sizes = W.log_uniform_sizes(batches, 10, 8192, seed=base + 300)
+        stream = W.undirected_update_stream(lo, hi, n, sizes, base + 301, gen.sample)
+        seeds = W.rng_for(base + 302).choice(n, S, replace=False).astype(np.int32)
+        desc = ("undirected Chung-Lu (exponent 2.1, mean degree 16), both directions stored; "
+                "batches of log-uniform 10..8192 undirected edges, half insertions")
+    else:
+        gen, src, dst = W.rmat_graph(log2n, m, seed=base)
+        seeds = W.rng_for(base + 302).choice(n, S, replace=False).astype(np.int32)
+        stream = W.node_op_stream(src, dst, n, batches, 1000, 8, 500, 500, base + 301,
+                                  protect=tuple(int(s) for s in seeds))
+        desc = ("directed R-MAT (a,b,c,d=.57,.19,.19,.05), ids permuted; batches of 10,000 ops: "
+                "500 edge ops, 1,000 new nodes x 8 out-edges, 500 node deletions")
+    config = {"workload": name if log2n == full else "%s_at_log2n_%d" % (name, log2n),
+              "graph": desc, "nodes": n, "edges": int(src.size), "seeds": S,
+              "seed_rule": "uniform", "c": C_RESTART, "eps": cfg["eps"],
+              "batches": len(stream), "gather_vectors": cfg["precision"], "sums": "fp64",
+              "inputs": "update batches resident in HBM before the timed region",
+              "l2": "working set (score block) larger than L2"}
+    return cfg, n, src, dst, seeds, stream, config
+
+
+def multi_alg_bytes(st, n, m, Sp, by):
+    """Algorithmic bytes of one seed-block launch: x(0) pass 4n (stamps) + n Sp b_y
+    (first gather block); each pull step 4m (in-list ids) + 12n (offset, length,
+    scale) + n Sp b_y (each source row gathered once) + n Sp b_y (next gather
+    block) + 16 n Sp (score block read and written)."""
+    steps = st["iterations"]
+    return 4 * n + n * Sp * by + steps * (4 * m + 12 * n + n * Sp * (2 * by + 16))
+
+
+def run_multi(args, rank, world):
+    import torch
+
+    from paper_1712_00595_gb300 import native as N
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, n, src, dst, seeds, stream, config = make_multi_workload(args.workload, args.log2n)
+    K = min(args.steps, len(stream) - 3)
+    Wm = min(args.warmup, len(stream) - K)
+    prec = {"fp32": N.OSP_PREC_FP32_ACC64, "bf16": N.OSP_PREC_BF16_ACC64}[cfg["precision"]]
+    by = {"fp32": 4, "bf16": 2}[cfg["precision"]]
+    S = len(seeds)
+    Sp = 32 * (1 if S <= 32 else 2 if S <= 64 else 4 if S <= 128 else 8)
+    offs = np.cumsum([0] + [b.size for b in stream])
+    ops_dev = torch.from_numpy(np.concatenate(stream).view(np.int32).copy()).to(dev)
+    base_ptr = ops_dev.data_ptr()
+    tstream = torch.cuda.Stream(device=dev)
+    eps = cfg["eps"]
+    eps_init = 1e-8
+    sample = np.linspace(0, S - 1, min(args.fp64_seeds, S)).astype(int) if args.fp64_seeds else []
+
+    def engine(p):
+        e = N.Engine(precision=p, device=local, stream=tstream.cuda_stream)
+        e.load_graph(n, src, dst)
+        e.set_seeds(seeds, C_RESTART)
+        return e
+
+    eng = engine(prec)
+    eng.init_scores(eps_init)
+    counts = [eng.get_seed_stats()[0].copy()]
+    for b in range(Wm):
+        eng.apply_updates_device(base_ptr + 12 * int(offs[b]), int(stream[b].size), eps)
+        counts.append(eng.get_seed_stats()[0].copy())
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stats = []
+    for k in range(K):
+        b = Wm + k
+        ev[k][0].record(tstream)
+        stats.append(eng.apply_updates_device(base_ptr + 12 * int(offs[b]), int(stream[b].size), eps))
+        ev[k][1].record(tstream)
+        counts.append(eng.get_seed_stats()[0].copy())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist_barrier(world)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    steps_us = eng.get_step_times()
+    r_s = {int(j): eng.query(int(j)) for j in sample}
+    eng.close()
+    t = dist_max(sum(ms) / 1e3, world)
+    value = world * K / t
+    prop_ms = sum(s["ms_propagate"] for s in stats)
+    ab = sum(multi_alg_bytes(s, s["n_nodes"], s["m_edges"], Sp, by) for s in stats)
+    peak, peak_kind = peaks()
+    step_bytes = 4 * stats[-1]["m_edges"] + 12 * stats[-1]["n_nodes"] + stats[-1]["n_nodes"] * Sp * (2 * by + 16)
+    med_step = float(np.median(steps_us[1:])) if len(steps_us) > 1 else float("nan")
+    out = {
+        "metric": METRIC, "value": value, "unit": "batches/s", "seed_batches_per_s": value * S,
+        "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": cfg["precision"], "accumulate": "f64", "data": "synthetic", "config": config,
+        "roofline": {"bound": "hbm", "achieved": ab / (prop_ms / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": ab / (prop_ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "kernel": "k_propagate_multi", "peak_kind": peak_kind + " (hbm_gbs copy)",
+                     "alg_bytes_per_launch": ab / K, "ms_per_launch": prop_ms / K,
+                     "pull_step": {"alg_bytes": step_bytes, "median_us": med_step,
+                                   "frac": step_bytes / (med_step * 1e-6) / 1e9 / peak}},
+        "phases_ms_per_step": {"update_merge_offset": sum(s["ms_update"] for s in stats) / K,
+                               "propagation": prop_ms / K},
+        "iterations_per_step": float(np.mean([s["iterations"] for s in stats])),
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "clocks": clk,
+        "last_step_profile_us": {"x0": float(steps_us[0]),
+                                 "steps": [round(float(x), 1) for x in steps_us[1:]]},
+    }
+    if len(sample):
+        # the plain FP64 path, replaying every seed's step counts (lock-step)
+        e64 = engine(N.OSP_PREC_FP64)
+        e64.set_seed_iterations(counts[0])
+        e64.init_scores(eps_init)
+        ms64 = []
+        for b in range(Wm + K):
+            e64.set_seed_iterations(counts[b + 1])
+            st = e64.apply_updates_device(base_ptr + 12 * int(offs[b]), int(stream[b].size), eps)
+            if b >= Wm:
+                ms64.append(st["ms_update"] + st["ms_propagate"])
+        l1s = [float(np.abs(r_s[j] - e64.query(j)).sum()) for j in r_s]
+        e64.close()
+        out["l1_vs_fp64"] = {"max": max(l1s), "mean": float(np.mean(l1s)), "seeds": len(l1s)}
+        out["fp64_path"] = {"value": K / (sum(ms64) / 1e3), "unit": "batches/s"}
+        out["speedup_vs_fp64"] = value / world / out["fp64_path"]["value"]
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload != "rmat20":
+        run_multi(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -234,6 +234,12 @@ osp_status osp_get_size(osp_ctx *ctx, int64_t *n, int64_t *m);
 osp_status osp_get_seed_stats(osp_ctx *ctx, int32_t *iterations, double *qoff_l1,
                               double *last_l1, int32_t cap, int32_t *count);
 
+/* Fix each seed's number of propagation steps for the following init/apply
+ * calls (k[j] > 0: seed j runs exactly k[j] steps; 0: its eps rule), to
+ * compare precisions step for step; k = NULL clears. S must equal the number of
+ * seeds. osp_set_fixed_iterations, when nonzero, takes precedence. */
+osp_status osp_set_seed_iterations(osp_ctx *ctx, const int32_t *k, int32_t S);
+
 /* ||x(0)||_1 .. ||x(k)||_1 of the last init/apply call (host, up to cap entries;
  * with several seeds each entry is the maximum over the seeds that ran the step). */
 osp_status osp_get_l1_history(osp_ctx *ctx, double *out, int32_t cap, int32_t *count);

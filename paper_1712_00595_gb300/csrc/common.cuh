@@ -27,6 +27,8 @@ constexpr int kPropThreads = 256;
 constexpr int kPropWarps = kPropThreads / 32;
 constexpr int kHubThreshold = 1024;  // pull step: in-lists longer than this are summed in pieces
 constexpr int kHubPiece = 1024;      // pull step: edges per hub piece
+constexpr int kMultiHub = 256;       // seed block: in-lists longer than this, in pieces of this size
+constexpr int kMultiNodeItems = 4;   // seed block: task items per node (a node's score row costs more)
 constexpr int kTaskItems = 1024;     // pull step: items (edges + nodes) per warp task
 constexpr double kPushAlpha = 14.0;  // push step while frontier out-edges <= m / alpha
 constexpr double kPushBeta = 24.0;   // ... and frontier size <= n / beta
@@ -51,6 +53,7 @@ struct Ctl {
   int n_mpieces;               // merge pieces of the current batch
   int dense0;                  // 1: x(0) is found by a dense scan of xacc (no queue from the merge)
   int n_opieces;               // several seeds: offset items (256 entries of a changed row)
+  int hub_thr, hub_piece;      // pull step: in-lists longer than hub_thr go in pieces of hub_piece
   int epoch;                   // frontier mark of x(0); step i uses epoch + i
   int q_size[2];               // frontier queue lengths
   unsigned int bar_count, bar_gen;
@@ -80,6 +83,7 @@ struct Multi {
   int* col_iters;      // [Sp] steps run per column
   double* col_q;       // [Sp] ||x(0)||_1 per column
   double* col_last;    // [Sp] ||x(k)||_1 at the column's stop
+  int* force;          // [Sp] > 0: the column runs exactly that many steps
   void* hub_acc;       // [hubs Sp] (float or double) partial sums of long in-lists
 };
 

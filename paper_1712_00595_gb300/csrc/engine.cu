@@ -42,6 +42,7 @@ struct osp_ctx {
   double c = 0.15;
   int grid_multi = 0;
   int grid_multi_init = 0;
+  int seed_force_max = 0;      // largest per-seed step count set by osp_set_seed_iterations
   std::vector<void*> mallocs;  // buffers of the seed block, freed when the seeds change
   int fixed_iters = 0;
   int grid_prop = 0;
@@ -112,6 +113,7 @@ void free_multi(osp_ctx* ctx) {
   ctx->mallocs.clear();
   ctx->d.mu = Multi{};
   ctx->S = 1;
+  ctx->seed_force_max = 0;
 }
 
 void free_all(osp_ctx* ctx) {
@@ -350,9 +352,11 @@ osp_status plan_pull(osp_ctx* ctx, int64_t n_bound, int64_t m_bound) {
   ++ctx->launches;
   k_scan_add<<<(ns + 255) / 256, 256, 0, st>>>(ctx->d.pc, ctx->scan_bsum, ns);
   ++ctx->launches;
-  k_pull_plan<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d);
+  const bool multi = ctx->S > 1;
+  k_pull_plan<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d, multi ? kMultiHub : kHubThreshold,
+                                                 multi ? kMultiNodeItems : 1);
   ++ctx->launches;
-  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d);
+  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d, multi ? kMultiHub : kHubPiece);
   ++ctx->launches;
   CK(cudaGetLastError());
   return OSP_OK;
@@ -365,6 +369,8 @@ osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_
   pp.max_iter = default_max_iter(ctx, eps);
   pp.force_iters = ctx->fixed_iters;
   if (pp.force_iters > pp.max_iter) pp.max_iter = std::min(pp.force_iters, kMaxHist - 1);
+  if (ctx->S > 1 && ctx->seed_force_max > pp.max_iter)
+    pp.max_iter = std::min(ctx->seed_force_max, kMaxHist - 1);
   pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : kPushAlpha;
   pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : kPushBeta;
   pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
@@ -660,16 +666,18 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
     AL(d.piece_base, npc, 0);
   }
   AL(d.pc, nc + 1, 0);
-  AL(d.task_first, (int64_t)(nc + (int64_t)cap) / kTaskItems + 2, 0);
+  AL(d.task_first, (int64_t)(kMultiNodeItems * nc + (int64_t)cap) / kTaskItems + 2, 0);
   {
-    // lists longer than kHubThreshold number at most (live edges) / kHubThreshold <= cap / kHubThreshold
-    const int64_t nh = (int64_t)(cap / kHubThreshold) + 2;
+    // lists longer than a threshold t number at most (live edges) / t <= cap / t;
+    // the pull plan uses t = kMultiHub for the seed block, kHubThreshold otherwise
+    const int64_t nh = (int64_t)(cap / kMultiHub) + 2;
     AL(d.hubs, nh, 0);
     AL(d.hub_pstart, nh + 1, 0);
     AL(d.hub_acc, nh, 0);
     AL(d.hub_cnt, nh, 0);
-    AL(d.big_u, nh, 0);
-    AL(d.big_y, nh, 0);
+    const int64_t nb = (int64_t)(cap / kHubThreshold) + 2;  // push: rows above kHubThreshold
+    AL(d.big_u, nb, 0);
+    AL(d.big_y, nb, 0);
   }
   AL(d.part_l1, kMaxGrid, 0);
   AL(d.part_ef, kMaxGrid, 0);
@@ -765,7 +773,7 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     const size_t cells = (size_t)ctx->nc * 32 * K;
     // bf16 batches keep float-sized gather blocks: the initial CPI runs in float
     const size_t ybytes = ctx->opt.precision == OSP_PREC_FP64 ? 8 : 4;
-    const size_t nh = (size_t)(ctx->cap_c / kHubThreshold) + 2;
+    const size_t nh = (size_t)(ctx->cap_c / kMultiHub) + 2;
     unsigned char* y0 = nullptr;
     unsigned char* y1 = nullptr;
     double* hub = nullptr;
@@ -787,6 +795,7 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     ML(M.col_iters, 32 * K);
     ML(M.col_q, 32 * K);
     ML(M.col_last, 32 * K);
+    ML(M.force, 32 * K);
     ML(hub, nh * 32 * K);
 #undef ML
     M.S = S;
@@ -1025,6 +1034,28 @@ osp_status osp_get_seed_stats(osp_ctx* ctx, int32_t* iterations, double* qoff_l1
   }
   CK(cudaStreamSynchronize(st));
   *count = k;
+  return OSP_OK;
+}
+
+osp_status osp_set_seed_iterations(osp_ctx* ctx, const int32_t* k, int32_t S) {
+  if (!ctx) return OSP_EINVAL;
+  if (!ctx->seeded) return fail(ctx, OSP_ESTATE, "no seed set");
+  if (k && S != ctx->S) return fail(ctx, OSP_EINVAL, "need one step count per seed");
+  for (int j = 0; k && j < S; ++j)
+    if (k[j] < 0 || k[j] >= kMaxHist) return fail(ctx, OSP_EINVAL, "step count out of range");
+  if (ctx->S == 1) {
+    ctx->fixed_iters = k ? k[0] : 0;
+    return OSP_OK;
+  }
+  CK(cudaSetDevice(ctx->device));
+  const Multi& M = ctx->d.mu;
+  std::vector<int32_t> f(M.Sp, 0);
+  for (int j = 0; k && j < S; ++j) f[j] = k[j];
+  int mx = 0;
+  for (int v : f) mx = std::max(mx, v);
+  ctx->seed_force_max = mx;
+  CK(cudaMemcpyAsync(M.force, f.data(), sizeof(int32_t) * M.Sp, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return OSP_OK;
 }
 

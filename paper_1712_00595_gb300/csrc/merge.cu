@@ -319,23 +319,27 @@ __global__ void k_merge_finish(Dev d) {
 }
 
 // Pull-step plan, part 1: warp task t starts at the first node v with
-// pc[v] + v >= t * kTaskItems (so a task holds about kTaskItems edges + nodes
-// and never splits a list); long in-lists are listed for piecewise summation.
-__global__ void k_pull_plan(Dev d) {
+// pc[v] + node_w v >= t * kTaskItems (so a task holds about kTaskItems items,
+// an edge counting 1 and a node node_w, and never splits a list); in-lists
+// longer than hub_thr are listed for piecewise summation.
+__global__ void k_pull_plan(Dev d, int hub_thr, int node_w) {
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   const int n = ctl->n;
-  const long long W = (long long)n + ctl->m;
+  const long long W = (long long)node_w * n + ctl->m;
   const int nt = (int)((W + kTaskItems - 1) / kTaskItems);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  if (tid == 0) ctl->n_tasks = nt;
+  if (tid == 0) {
+    ctl->n_tasks = nt;
+    ctl->hub_thr = hub_thr;
+  }
   for (int t = tid; t <= nt; t += nth) {
     const long long target = (long long)t * kTaskItems;
     int lo = 0, hi = n;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if ((long long)d.pc[mid] + mid < target) lo = mid + 1;
+      if ((long long)d.pc[mid] + (long long)node_w * mid < target) lo = mid + 1;
       else hi = mid;
     }
     d.task_first[t] = t == nt ? n : lo;
@@ -343,13 +347,13 @@ __global__ void k_pull_plan(Dev d) {
   const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += nth) {
     const int v = base + lane;
-    const bool h = v < n && d.len_c[v] > kHubThreshold;
+    const bool h = v < n && d.len_c[v] > hub_thr;
     warp_append(h, v, d.hubs, &ctl->n_hubs);
   }
 }
 
 // Pull-step plan, part 2 (one CTA): piece prefix over the long in-lists.
-__global__ void __launch_bounds__(1024) k_hub_prefix(Dev d) {
+__global__ void __launch_bounds__(1024) k_hub_prefix(Dev d, int hub_piece) {
   __shared__ int s_w[32];
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(1024) k_hub_prefix(Dev d) {
   const int per = (nh + 1023) / 1024;
   const int lo = min(nh, tid * per), hi = min(nh, lo + per);
   int mine = 0;
-  for (int h = lo; h < hi; ++h) mine += (d.len_c[d.hubs[h]] + kHubPiece - 1) / kHubPiece;
+  for (int h = lo; h < hi; ++h) mine += (d.len_c[d.hubs[h]] + hub_piece - 1) / hub_piece;
   int x = mine;
   for (int o = 1; o < 32; o <<= 1) {
     int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -378,13 +382,14 @@ __global__ void __launch_bounds__(1024) k_hub_prefix(Dev d) {
   int base = (w ? s_w[w - 1] : 0) + x - mine;
   for (int h = lo; h < hi; ++h) {
     d.hub_pstart[h] = base;
-    base += (d.len_c[d.hubs[h]] + kHubPiece - 1) / kHubPiece;
+    base += (d.len_c[d.hubs[h]] + hub_piece - 1) / hub_piece;
     d.hub_acc[h] = 0.0;
     d.hub_cnt[h] = 0;
   }
   if (tid == 0) {
     d.hub_pstart[nh] = s_w[31];
     ctl->n_pieces = s_w[31];
+    ctl->hub_piece = hub_piece;
   }
 }
 

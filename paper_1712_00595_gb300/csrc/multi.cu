@@ -97,11 +97,31 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
   const Multi& M = d.mu;
   Ctl* ctl = d.ctl;
   __shared__ double s_max[kPropThreads / 32];
+  __shared__ double s_sum[kPropThreads];
+  // thread t sums column t % Sp over the CTAs b = t / Sp (mod Q) with eight
+  // independent accumulators; the Q slices are then added in a fixed order
+  const int Q = (int)blockDim.x / Sp;
+  const int G = (int)gridDim.x;
+  {
+    const int jc = threadIdx.x % Sp, q = threadIdx.x / Sp;
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 0.0;
+    for (int b = q; b < G; b += 8 * Q) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int bb = b + u * Q;
+        if (bb < G) a[u] += __ldcg(M.part + (size_t)bb * Sp + jc);
+      }
+    }
+    s_sum[threadIdx.x] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  }
+  __syncthreads();
   double seen = 0.0;
   int live = 0;
   for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
     double L = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) L += __ldcg(M.part + (size_t)b * Sp + j);
+    for (int q = 0; q < Q; ++q) L += s_sum[q * Sp + j];
     if (j >= M.S) continue;
     if (it == 0) {
       M.col_q[j] = L;
@@ -114,7 +134,8 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
       M.col_iters[j] = it;
       M.col_last[j] = L;
       seen = fmax(seen, L);
-      int stop = pp.force_iters > 0 ? it >= pp.force_iters : L <= pp.eps;
+      const int f = pp.force_iters > 0 ? pp.force_iters : M.force[j];
+      int stop = f > 0 ? it >= f : L <= pp.eps;
       if (!stop && it >= pp.max_iter) {
         stop = 1;
         ctl->noconv = 1;
@@ -143,17 +164,16 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
   }
 }
 
-// x(i)[v] from the K-column sums acc: add into R for running columns, write
-// the next gather row (zero for stopped columns), accumulate |x|.
+// x(i)[v] from the K-column sums acc: add into R for running columns (rr is
+// the row of R, loaded before the sums), write the next gather row (zero for
+// stopped columns), accumulate |x|.
 template <typename TY, int K, typename A>
-__device__ __forceinline__ void finish_row(const Dev& d, int v, const A (&acc)[K], unsigned act,
-                                           TY* yd, double (&l1)[K]) {
+__device__ __forceinline__ void finish_row(const Dev& d, int v, const A (&acc)[K], A s,
+                                           double (&rr)[K], unsigned act, TY* yd,
+                                           double (&l1)[K]) {
   constexpr int Sp = 32 * K;
   const int lane = threadIdx.x & 31;
   const size_t base = (size_t)v * Sp + lane * K;
-  const A s = std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
-  alignas(16) double rr[K];
-  load_cg(d.mu.r + base, rr);
   alignas(16) TY yv[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -170,28 +190,47 @@ __device__ __forceinline__ void finish_row(const Dev& d, int v, const A (&acc)[K
   store_k(yd + base, yv);
 }
 
-// Sum of y rows over in-list entries p[0 .. len), four rows in flight.
+template <typename A>
+__device__ __forceinline__ A scale_of(const Dev& d, int v) {
+  return std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
+}
+
+// Sum of y rows over in-list entries p[0 .. len): 32 ids per coalesced load,
+// then up to eight rows in flight.
 template <typename TY, int K, typename A>
-__device__ __forceinline__ void sum_rows(const int* p, int len, const TY* ys, A (&acc)[K]) {
+__device__ __forceinline__ void sum_rows(const int* p, int len, const TY* ys, A (&acc)[K],
+                                         int idx0 = -1) {
   constexpr int Sp = 32 * K;
   const int lane = threadIdx.x & 31;
   for (int b = 0; b < len; b += 32) {
     const int cnt = min(32, len - b);
-    const int idx = lane < cnt ? __ldg(p + b + lane) : 0;
+    // ids of the first block may come preloaded (idx0 >= 0 on every lane)
+    const int idx = (b == 0 && __all_sync(0xffffffffu, idx0 >= 0)) ? idx0
+                    : (lane < cnt ? __ldg(p + b + lane) : 0);
     int j = 0;
-    for (; j + 4 <= cnt; j += 4) {
-      const int u0 = __shfl_sync(0xffffffffu, idx, j);
-      const int u1 = __shfl_sync(0xffffffffu, idx, j + 1);
-      const int u2 = __shfl_sync(0xffffffffu, idx, j + 2);
-      const int u3 = __shfl_sync(0xffffffffu, idx, j + 3);
-      alignas(16) TY a0[K], a1[K], a2[K], a3[K];
-      load_cg(ys + (size_t)u0 * Sp + lane * K, a0);
-      load_cg(ys + (size_t)u1 * Sp + lane * K, a1);
-      load_cg(ys + (size_t)u2 * Sp + lane * K, a2);
-      load_cg(ys + (size_t)u3 * Sp + lane * K, a3);
+    for (; j + 8 <= cnt; j += 8) {
+      alignas(16) TY a[8][K];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int u = __shfl_sync(0xffffffffu, idx, j + q);
+        load_cg(ys + (size_t)u * Sp + lane * K, a[q]);
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k)
-        acc[k] += (to_acc(a0[k]) + to_acc(a1[k])) + (to_acc(a2[k]) + to_acc(a3[k]));
+        acc[k] += ((to_acc(a[0][k]) + to_acc(a[1][k])) + (to_acc(a[2][k]) + to_acc(a[3][k]))) +
+                  ((to_acc(a[4][k]) + to_acc(a[5][k])) + (to_acc(a[6][k]) + to_acc(a[7][k])));
+    }
+    if (j + 4 <= cnt) {
+      alignas(16) TY a[4][K];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = __shfl_sync(0xffffffffu, idx, j + q);
+        load_cg(ys + (size_t)u * Sp + lane * K, a[q]);
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        acc[k] += (to_acc(a[0][k]) + to_acc(a[1][k])) + (to_acc(a[2][k]) + to_acc(a[3][k]));
+      j += 4;
     }
     for (; j < cnt; ++j) {
       const int u = __shfl_sync(0xffffffffu, idx, j);
@@ -332,6 +371,7 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
   const int n_hubs = ctl->n_hubs;
   const int n_pieces = ctl->n_pieces;
   const int n_tasks = ctl->n_tasks;
+  const int hub_thr = ctl->hub_thr, hub_piece = ctl->hub_piece;
   TY* yb[2] = {(TY*)M.y0, (TY*)M.y1};
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -343,14 +383,19 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
     double l1[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) l1[k] = 0.0;
-    for (int v = gw; v < n; v += nw) {
+    for (int vb = gw * 32; vb < n; vb += nw * 32) {
+     const int vl = vb + lane;
+     const unsigned stamped = __ballot_sync(0xffffffffu, vl < n && __ldcg(d.mark + vl) == epoch);
+     const int cnt = min(32, n - vb);
+     for (int jj = 0; jj < cnt; ++jj) {
+      const int v = vb + jj;
       const size_t base = (size_t)v * Sp + lane * K;
       alignas(16) TY yv[K];
-      if (__ldcg(d.mark + v) == epoch) {
+      if ((stamped >> jj) & 1u) {
         alignas(16) double x[K], rr[K], z[K];
         load_cg(M.xacc + base, x);
         load_cg(M.r + base, rr);
-        const A s = std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
+        const A s = scale_of<A>(d, v);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           rr[k] += x[k];
@@ -365,6 +410,7 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
         for (int k = 0; k < K; ++k) yv[k] = from_acc((A)0, (TY*)nullptr);
       }
       store_k(yb[0] + base, yv);
+     }
     }
     column_partials<K>(M, l1, s_part);
     if (bar_arrive(ctl, sh)) decide_multi<K>(d, pp, 0, m);
@@ -400,8 +446,8 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
         const int v = __ldg(d.hubs + h);
         const int piece = t - __ldg(d.hub_pstart + h);
         const int full = __ldg(d.len_c + v);
-        const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
-        const int L = min(kHubPiece, full - piece * kHubPiece);
+        const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * hub_piece);
+        const int L = min(hub_piece, full - piece * hub_piece);
         A acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = (A)0;
@@ -412,7 +458,7 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
         __threadfence();
         int last = 0;
         if (lane == 0) {
-          const int np = (full + kHubPiece - 1) / kHubPiece;
+          const int np = (full + hub_piece - 1) / hub_piece;
           last = atomicAdd(&d.hub_cnt[h], 1) == np - 1;
         }
         last = __shfl_sync(0xffffffffu, last, 0);
@@ -424,20 +470,70 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
             ha[k] = (A)0;
           }
           if (lane == 0) d.hub_cnt[h] = 0;
-          finish_row<TY, K, A>(d, v, acc, act, yd, l1);
+          alignas(16) double rr[K];
+          load_cg(M.r + (size_t)v * Sp + lane * K, rr);
+          finish_row<TY, K, A>(d, v, acc, scale_of<A>(d, v), rr, act, yd, l1);
         }
         continue;
       }
       const int task = t - n_pieces;
       const int c0 = __ldg(d.task_first + task), c1 = __ldg(d.task_first + task + 1);
-      for (int v = c0; v < c1; ++v) {
-        const int len = __ldg(d.len_c + v);
-        if (len > kHubThreshold) continue;  // summed in pieces
-        A acc[K];
+      for (int vb = c0; vb < c1; vb += 32) {
+        // offsets and lengths of up to 32 consecutive nodes in one coalesced load
+        const int vl = vb + lane;
+        int my_len = 0;
+        unsigned my_off = 0;
+        if (vl < c1) {
+          my_len = __ldg(d.len_c + vl);
+          my_off = __ldg(d.off_c + vl);
+        }
+        const int cnt = min(32, c1 - vb);
+        // empty in-lists: x(i)[v] = 0, R unchanged, the next gather row is zero
+        unsigned empty = __ballot_sync(0xffffffffu, lane < cnt && my_len == 0);
+        while (empty) {
+          const int jj = __ffs(empty) - 1;
+          empty &= empty - 1;
+          alignas(16) TY z[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = (A)0;
-        sum_rows<TY, K, A>(d.pool_c + __ldg(d.off_c + v), len, ys, acc);
-        finish_row<TY, K, A>(d, v, acc, act, yd, l1);
+          for (int k = 0; k < K; ++k) z[k] = from_acc((A)0, (TY*)nullptr);
+          store_k(yd + (size_t)(vb + jj) * Sp + lane * K, z);
+        }
+        // the others (hubs excepted) in order, two deep: the first 32 in-list ids
+        // and the row of R of the next node load while the current one is summed
+        unsigned todo = __ballot_sync(0xffffffffu, lane < cnt && my_len > 0 && my_len <= hub_thr);
+        if (!todo) continue;
+        int jn = __ffs(todo) - 1;
+        todo &= todo - 1;
+        int len_n = __shfl_sync(0xffffffffu, my_len, jn);
+        unsigned off_n = __shfl_sync(0xffffffffu, my_off, jn);
+        int idx_n = lane < len_n ? __ldg(d.pool_c + off_n + lane) : 0;
+        alignas(16) double rr_n[K];
+        load_cg(M.r + (size_t)(vb + jn) * Sp + lane * K, rr_n);
+        for (;;) {
+          const int jc = jn, len = len_n;
+          const unsigned off = off_n;
+          const int idx = idx_n;
+          alignas(16) double rr[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) rr[k] = rr_n[k];
+          const bool more = todo != 0;
+          if (more) {
+            jn = __ffs(todo) - 1;
+            todo &= todo - 1;
+            len_n = __shfl_sync(0xffffffffu, my_len, jn);
+            off_n = __shfl_sync(0xffffffffu, my_off, jn);
+            idx_n = lane < len_n ? __ldg(d.pool_c + off_n + lane) : 0;
+            load_cg(M.r + (size_t)(vb + jn) * Sp + lane * K, rr_n);
+          }
+          const int v = vb + jc;
+          const A s = scale_of<A>(d, v);
+          A acc[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[k] = (A)0;
+          sum_rows<TY, K, A>(d.pool_c + off, len, ys, acc, idx);
+          finish_row<TY, K, A>(d, v, acc, s, rr, act, yd, l1);
+          if (!more) break;
+        }
       }
     }
     column_partials<K>(M, l1, s_part);

@@ -251,7 +251,7 @@ __device__ __forceinline__ void finish_node(const Dev& d, int v, double x, void*
 // piece that completes a list finishes it).
 template <typename T>
 __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_pieces,
-                            int n_tasks, T* wacc, int* grab) {
+                            int n_tasks, T* wacc, int* grab, int hub_thr, int hub_piece) {
   constexpr bool kF32 = std::is_same<T, float>::value;
   double l1 = 0.0;
   const int lane = threadIdx.x & 31;
@@ -281,8 +281,8 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
       const int v = __ldg(d.hubs + h);
       const int piece = t - __ldg(d.hub_pstart + h);
       const int full = __ldg(d.len_c + v);
-      const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * kHubPiece);
-      const int L = min(kHubPiece, full - piece * kHubPiece);
+      const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * hub_piece);
+      const int L = min(hub_piece, full - piece * hub_piece);
       T acc = (T)0;
       int j = lane;
       for (; j + 96 < L; j += 128) {
@@ -295,7 +295,7 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
       if (lane == 0) {
         atomicAdd(&d.hub_acc[h], (double)acc);
         __threadfence();
-        const int np = (full + kHubPiece - 1) / kHubPiece;
+        const int np = (full + hub_piece - 1) / hub_piece;
         if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
           __threadfence();
           const double x =
@@ -317,7 +317,7 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
         o = __ldg(d.off_c + v);
         len = __ldg(d.len_c + v);
       }
-      const bool hub = len > kHubThreshold;
+      const bool hub = len > hub_thr;
       const bool light = len <= kLight;
       // the chunk's short lists as one flattened edge stream: 32 consecutive
       // edges per round, coalesced index loads; edge e belongs to the lane l
@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
   const int n_hubs = ctl->n_hubs;
   const int n_pieces = ctl->n_pieces;
   const int n_tasks = ctl->n_tasks;
+  const int hub_thr = ctl->hub_thr, hub_piece = ctl->hub_piece;
   T* yb[2] = {(T*)d.y0, (T*)d.y1};
   int* qb[2] = {d.q0, d.q1};
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
       }
     } else {
       l1 = pull_step<T>(d, yb[src], yb[dst], n_hubs, n_pieces, n_tasks,
-                        s_wacc + (threadIdx.x & ~31), &ctl->ctr[1]);
+                        s_wacc + (threadIdx.x & ~31), &ctl->ctr[1], hub_thr, hub_piece);
     }
     block_partials(d, l1, ef, s_l1, s_ef);
     if (bar_arrive(ctl, sh)) decide(d, pp, mode, n, m, s_l1, s_ef);

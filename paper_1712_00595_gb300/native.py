@@ -30,6 +30,7 @@ EXPORTED = [
     "osp_query", "osp_query_device", "osp_topk", "osp_export_graph", "osp_get_size",
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
     "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
+    "osp_set_seed_iterations",
 ]
 
 
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
             "osp_status_string": (C.c_char_p, [C.c_int]),
             "osp_topk_noalloc": (C.c_int, [P, i64, i32, C.c_int, P, P, P, P]),
             "osp_get_seed_stats": (C.c_int, [P, P, P, P, i32, P]),
+            "osp_set_seed_iterations": (C.c_int, [P, P, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -242,6 +244,13 @@ class Engine:
         cnt = C.c_int32(0)
         self._check(self._L.osp_get_l1_history(self._h, _ptr(out), int(cap), C.byref(cnt)))
         return out[: cnt.value]
+
+    def set_seed_iterations(self, k=None):
+        """Per-seed step counts for the following calls (None clears)."""
+        if k is None:
+            return self._check(self._L.osp_set_seed_iterations(self._h, None, 0))
+        k = np.ascontiguousarray(k, np.int32)
+        return self._check(self._L.osp_set_seed_iterations(self._h, _ptr(k), int(k.size)))
 
     def get_seed_stats(self, cap=256):
         """Per seed of the last call: (steps run, ||x(0)||_1, ||x(k)||_1 at its stop)."""

@@ -119,6 +119,55 @@ class RMat:
         return split_keys(_fill_unique(draw, m, 1 << 24))
 
 
+class ChungLu:
+    """Chung-Lu power-law sampler over n nodes (undirected pairs).
+
+    Node i (before relabelling) has weight w_i proportional to
+    (i + 1) ** (-1 / (beta - 1)), scaled so that the weights sum to
+    mean_degree * n and capped at sqrt(sum w); an edge's endpoints are drawn
+    independently with probability proportional to w. Ids are relabelled by a
+    seeded permutation, as for R-MAT.
+    """
+
+    def __init__(self, n: int, mean_degree: float = 16.0, beta: float = 2.1,
+                 seed: int = BASE_SEED):
+        self.n = n
+        self.rng = rng_for(seed)
+        w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (beta - 1.0))
+        w *= mean_degree * n / w.sum()
+        w = np.minimum(w, np.sqrt(w.sum()))
+        self.cdf = np.cumsum(w)
+        self.cdf /= self.cdf[-1]
+        self.perm = self.rng.permutation(n).astype(np.int64)
+
+    def sample(self, k: int):
+        u = np.searchsorted(self.cdf, self.rng.random(k), side="right")
+        v = np.searchsorted(self.cdf, self.rng.random(k), side="right")
+        u = np.minimum(u, self.n - 1)
+        v = np.minimum(v, self.n - 1)
+        return self.perm[u], self.perm[v]
+
+    def graph(self, m_undirected: int):
+        """m_undirected distinct unordered pairs {u, v}, u != v, returned as
+        (lo, hi) arrays (the caller stores both directions)."""
+        def draw(k):
+            out = []
+            for s in range(0, k, 1 << 24):
+                u, v = self.sample(min(1 << 24, k - s))
+                ok = u != v
+                lo, hi = np.minimum(u[ok], v[ok]), np.maximum(u[ok], v[ok])
+                out.append(edge_keys(lo, hi))
+            return np.concatenate(out)
+
+        return split_keys(_fill_unique(draw, m_undirected, 1 << 24))
+
+
+def chung_lu_graph(n: int, m_undirected: int, seed: int = BASE_SEED, **kw):
+    g = ChungLu(n, seed=seed, **kw)
+    lo, hi = g.graph(m_undirected)
+    return g, lo, hi
+
+
 def rmat_graph(scale: int, m: int, seed: int = BASE_SEED, **kw):
     g = RMat(scale, seed=seed, **kw)
     src, dst = g.graph(m)
@@ -258,3 +307,108 @@ def random_mixed_batch(rng, n: int, es: EdgeSet, dead: np.ndarray, n_ops: int,
     keys = np.array(sorted(cur_keys), dtype=np.uint64)
     es.keys = keys
     return out, nn
+
+
+def undirected_update_stream(lo, hi, n: int, sizes, seed: int, sampler):
+    """One batch per entry of ``sizes``: that many undirected pairs, half
+    insertions of absent pairs drawn from ``sampler`` and half deletions of
+    present pairs (uniform), each pair as its two directed ops."""
+    rng = rng_for(seed)
+    es = EdgeSet(lo, hi)  # canonical (min, max) keys
+    out = []
+    for k in sizes:
+        n_ins = int(k) // 2
+        n_del = int(k) - n_ins
+
+        def canon(kk):
+            u, v = sampler(kk)
+            return np.minimum(u, v), np.maximum(u, v)
+
+        ins = _draw_absent(es, n_ins, canon, rng)
+        dels = _draw_present(es, n_del, rng)
+        iu, iv = split_keys(ins)
+        du, dv = split_keys(dels)
+        ops = np.empty(2 * (ins.size + dels.size), UPDATE_DTYPE)
+        ops["u"] = np.concatenate([iu, iv, du, dv])
+        ops["v"] = np.concatenate([iv, iu, dv, du])
+        ops["op"] = np.concatenate([np.full(2 * ins.size, OP_INSERT_EDGE, np.int32),
+                                    np.full(2 * dels.size, OP_DELETE_EDGE, np.int32)])
+        out.append(ops[rng.permutation(ops.size)])
+        es.apply(ins, dels)
+    return out
+
+
+def log_uniform_sizes(batches: int, lo: float, hi: float, seed: int):
+    """floor(10 ** U(log10 lo, log10 hi)) per batch."""
+    rng = rng_for(seed)
+    return np.floor(10.0 ** rng.uniform(np.log10(lo), np.log10(hi), batches)).astype(np.int64)
+
+
+def node_op_stream(src, dst, n: int, batches: int, n_new: int, new_degree: int, n_del_nodes: int,
+                   n_edge_ops: int, seed: int, protect=()):
+    """Batches mixing node and edge operations, valid in sequence:
+    ``n_edge_ops`` edge ops (half insertions of absent edges between live
+    nodes, half deletions of present edges), then ``n_new`` node additions each
+    followed by ``new_degree`` out-edges to distinct live targets (uniform),
+    then ``n_del_nodes`` deletions of nodes that existed before the batch
+    (uniform over live nodes, never one in ``protect``)."""
+    rng = rng_for(seed)
+    es = EdgeSet(src, dst)
+    cap = n + batches * n_new + 8
+    dead = np.zeros(cap, bool)
+    guard = np.zeros(cap, bool)
+    guard[list(protect)] = True
+    nn = n
+    out = []
+    for _ in range(batches):
+        parts = []
+        # edge ops between live nodes
+        k_ins = n_edge_ops // 2
+        k_del = n_edge_ops - k_ins
+
+        def live_pairs(k):
+            u = rng.integers(0, nn, k, dtype=np.int64)
+            v = rng.integers(0, nn, k, dtype=np.int64)
+            ok = ~dead[u] & ~dead[v]
+            return u[ok], v[ok]
+
+        ins = _draw_absent(es, k_ins, live_pairs, rng)
+        dels = np.empty(0, np.uint64)
+        while dels.size < k_del:
+            cand = es.keys[rng.integers(0, es.keys.size, 2 * (k_del - dels.size) + 16)]
+            cu, cv = split_keys(cand)
+            cand = cand[~dead[cu] & ~dead[cv]]
+            dels = _first_unique(np.concatenate([dels, cand]))
+            dels = dels[~np.isin(dels, ins)]
+        dels = dels[:k_del]
+        parts.append(_pack(ins, dels, rng))
+        es.apply(ins, dels)
+        # new nodes with their out-edges
+        new_keys = []
+        for i in range(n_new):
+            w = nn + i
+            add = np.zeros(1, UPDATE_DTYPE)
+            add["op"] = OP_ADD_NODE
+            parts.append(add)
+            tg = np.empty(0, np.int64)
+            while tg.size < new_degree:
+                c = rng.integers(0, nn, 2 * new_degree, dtype=np.int64)
+                c = c[~dead[c]]
+                tg = np.unique(np.concatenate([tg, c]))
+            tg = rng.permutation(tg)[:new_degree]
+            e = np.zeros(new_degree, UPDATE_DTYPE)
+            e["u"], e["v"], e["op"] = w, tg, OP_INSERT_EDGE
+            parts.append(e)
+            new_keys.append(edge_keys(np.full(new_degree, w), tg))
+        nn += n_new
+        es.apply(np.concatenate(new_keys) if new_keys else np.empty(0, np.uint64),
+                 np.empty(0, np.uint64))
+        # node deletions among the nodes that existed before the batch
+        cand = np.flatnonzero(~dead[: nn - n_new] & ~guard[: nn - n_new])
+        victims = rng.choice(cand, n_del_nodes, replace=False)
+        dn = np.zeros(n_del_nodes, UPDATE_DTYPE)
+        dn["u"], dn["op"] = victims, OP_DELETE_NODE
+        parts.append(dn)
+        dead[victims] = True
+        out.append(np.concatenate(parts))
+    return out

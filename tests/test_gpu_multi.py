@@ -129,6 +129,25 @@ def test_multi_osp_sequence_all_op_kinds(prec):
     eng.close()
 
 
+def test_multi_seed_iterations_fixed_per_seed():
+    rng = np.random.default_rng(11)
+    n = 800
+    src, dst = hub_graph(rng, n, 6000, 0, 200, 3)
+    seeds = np.array([0, 10, 20, 30, 40], np.int32)
+    eng = make_engine(N.OSP_PREC_FP32_ACC64, n, src, dst, seeds, 1e-10)
+    want = np.array([1, 3, 7, 2, 5], np.int32)
+    eng.set_seed_iterations(want)
+    stream = W.edge_update_stream(src, dst, n, 2, 30, 20, seed=5)
+    st = eng.apply_updates(stream[0], 1e-3)
+    iters, _, _ = eng.get_seed_stats()
+    assert np.array_equal(iters, want) and st["iterations"] == 7
+    eng.set_seed_iterations(None)  # back to each seed's eps rule
+    eng.apply_updates(stream[1], 1e-3)
+    iters, _, last = eng.get_seed_stats()
+    assert np.all(iters >= 1) and np.all(last <= 1e-3)
+    eng.close()
+
+
 def test_multi_query_topk_columns():
     rng = np.random.default_rng(8)
     n = 3000
