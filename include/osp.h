@@ -97,6 +97,10 @@ typedef struct {
     int32_t node_order; /* internal node order: 0 = the caller's ids, 1 = descending
                            out-degree of the loaded graph. Results are the same up to
                            rounding order; every call uses the caller's ids. */
+    int32_t use_graphs; /* != 0: each apply call replays its kernel sequence from CUDA
+                           graphs (one pair per batch-size bucket, eps and fixed step counts,
+                           captured on first use and rebuilt when device buffers move),
+                           which removes most host launch work per batch. */
 } osp_options;
 
 /* Per-call statistics (the columns of Table 2 plus bookkeeping). */

@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -17,6 +19,10 @@ using namespace osp;
 namespace {
 
 constexpr int kIngestSmem = kMaxBatch * 8;
+// pinned staging: host ops of a batch first, then the batch size for graph replays
+constexpr size_t kPinnedBytes = 256 * 1024;
+constexpr size_t kPinnedBatchSize = sizeof(osp_update) * kMaxBatch;
+static_assert(kPinnedBatchSize + 64 <= kPinnedBytes, "pinned staging too small");
 
 struct HostCtlView {  // the leading fields of Ctl, read back after every call
   Ctl c;
@@ -43,6 +49,13 @@ struct osp_ctx {
   int grid_multi = 0;
   int grid_multi_init = 0;
   int seed_force_max = 0;      // largest per-seed step count set by osp_set_seed_iterations
+  // CUDA graphs of the batch path, by (ingest shared-memory bucket, eps, fixed
+  // step counts); dropped whenever device buffers move
+  struct GraphPair {
+    cudaGraphExec_t update = nullptr, propagate = nullptr;
+    int launches = 0;
+  };
+  std::map<std::tuple<int, double, int, int>, GraphPair> graphs;
   std::vector<void*> mallocs;  // buffers of the seed block, freed when the seeds change
   int fixed_iters = 0;
   int grid_prop = 0;
@@ -107,8 +120,17 @@ osp_status dalloc(osp_ctx* ctx, T** p, size_t count, int fill = 0,
   return OSP_OK;
 }
 
+void drop_graphs(osp_ctx* ctx) {
+  for (auto& kv : ctx->graphs) {
+    if (kv.second.update) cudaGraphExecDestroy(kv.second.update);
+    if (kv.second.propagate) cudaGraphExecDestroy(kv.second.propagate);
+  }
+  ctx->graphs.clear();
+}
+
 void free_multi(osp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx);
   for (void* p : ctx->mallocs) cudaFree(p);
   ctx->mallocs.clear();
   ctx->d.mu = Multi{};
@@ -248,6 +270,7 @@ osp_status compact(osp_ctx* ctx, bool rows) {
   }
   std::swap(pool, ctx->pool_spare);
   std::swap(cap, ctx->spare_cap);
+  drop_graphs(ctx);  // captured kernels hold the old pool pointers
   Ctl h;
   osp_status s = read_ctl(ctx, &h);
   if (s != OSP_OK) return s;
@@ -362,8 +385,7 @@ osp_status plan_pull(osp_ctx* ctx, int64_t n_bound, int64_t m_bound) {
   return OSP_OK;
 }
 
-osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_bound,
-                           bool init = false) {
+PropParams prop_params(osp_ctx* ctx, double eps) {
   PropParams pp;
   pp.eps = eps;
   pp.max_iter = default_max_iter(ctx, eps);
@@ -374,9 +396,11 @@ osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_
   pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : kPushAlpha;
   pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : kPushBeta;
   pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
-  osp_status s = plan_pull(ctx, n_bound, m_bound);
-  if (s != OSP_OK) return s;
-  CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  return pp;
+}
+
+// The persistent propagation kernel of one call.
+osp_status enqueue_propagate(osp_ctx* ctx, const PropParams& pp, bool init) {
   if (ctx->S > 1) {
     // bf16 gather vectors carry the small offsets of batches; the initial CPI
     // (total mass 1) runs with float gather vectors
@@ -389,6 +413,17 @@ osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_
   else
     CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
   ++ctx->launches;
+  return OSP_OK;
+}
+
+osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_bound,
+                           bool init = false) {
+  const PropParams pp = prop_params(ctx, eps);
+  osp_status s = plan_pull(ctx, n_bound, m_bound);
+  if (s != OSP_OK) return s;
+  CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  s = enqueue_propagate(ctx, pp, init);
+  if (s != OSP_OK) return s;
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
   return OSP_OK;
 }
@@ -404,21 +439,13 @@ osp_status check_ready(osp_ctx* ctx, bool need_scores) {
   return OSP_OK;
 }
 
-osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, double eps,
-                        osp_batch_stats* st) {
-  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
-  ctx->launches = 0;
-  osp_status s = reserve_for_batch(ctx, U);
-  if (s != OSP_OK) return s;
-  const int64_t m_before = ctx->m;
+// Ingest, merge and offset of one batch (U < 0: k_ingest reads the size from
+// the control block, as a graph replay does).
+osp_status enqueue_update(osp_ctx* ctx, const osp_update* ops_dev, int U, int Np) {
   const int g = ctx->num_sms * 4;
-  const int N = (int)std::max<int64_t>(2, U);
-  int Np = 2;
-  while (Np < N) Np <<= 1;
-  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
   k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;
-  k_ingest<<<1, 1024, (size_t)Np * 8, ctx->stream>>>(ctx->d, ops_dev, (int)U);
+  k_ingest<<<1, 1024, (size_t)Np * 8, ctx->stream>>>(ctx->d, ops_dev, U);
   ++ctx->launches;
   k_expand<<<g, 256, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;
@@ -438,6 +465,81 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
     ++ctx->launches;
   }
   CK(cudaGetLastError());
+  return OSP_OK;
+}
+
+// Capture the batch path for this bucket, eps and step settings.
+osp_status capture_graphs(osp_ctx* ctx, int Np, double eps, osp_ctx::GraphPair* out) {
+  cudaStream_t st = ctx->stream;
+  const int before = ctx->launches;
+  ctx->launches = 0;
+  const PropParams pp = prop_params(ctx, eps);
+  for (int part = 0; part < 2; ++part) {
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    osp_status s = OSP_OK;
+    if (part == 0) {
+      s = enqueue_update(ctx, ctx->ops_stage, -1, Np);
+      if (s == OSP_OK) s = plan_pull(ctx, ctx->nc - 1, 0);  // every node slot: fixed grids
+    } else {
+      s = enqueue_propagate(ctx, pp, false);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != OSP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    cudaGraphExec_t x = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    (part == 0 ? out->update : out->propagate) = x;
+  }
+  out->launches = ctx->launches;
+  ctx->launches = before;
+  return OSP_OK;
+}
+
+osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, double eps,
+                        osp_batch_stats* st) {
+  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  ctx->launches = 0;
+  osp_status s = reserve_for_batch(ctx, U);
+  if (s != OSP_OK) return s;
+  const int64_t m_before = ctx->m;
+  const int N = (int)std::max<int64_t>(2, U);
+  int Np = 2;
+  while (Np < N) Np <<= 1;
+  if (ctx->opt.use_graphs) {
+    if (U > 0 && ops_dev != ctx->ops_stage)
+      CK(cudaMemcpyAsync(ctx->ops_stage, ops_dev, sizeof(osp_update) * (size_t)U,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    int* pu = (int*)((char*)ctx->pinned + kPinnedBatchSize);
+    *pu = (int)U;
+    CK(cudaMemcpyAsync(&ctx->d.ctl->batch_U, pu, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    const auto key = std::make_tuple(Np, eps, ctx->fixed_iters, ctx->seed_force_max);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+      osp_ctx::GraphPair gp;
+      s = capture_graphs(ctx, Np, eps, &gp);
+      if (s != OSP_OK) {
+        if (gp.update) cudaGraphExecDestroy(gp.update);
+        return s;
+      }
+      it = ctx->graphs.emplace(key, gp).first;
+    }
+    CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+    CK(cudaGraphLaunch(it->second.update, ctx->stream));
+    CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    CK(cudaGraphLaunch(it->second.propagate, ctx->stream));
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    ctx->launches = it->second.launches;
+    return finish_call(ctx, m_before, st);
+  }
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  s = enqueue_update(ctx, ops_dev, (int)U, Np);
+  if (s != OSP_OK) return s;
   s = run_propagation(ctx, eps, std::min<int64_t>(ctx->n + U, ctx->nc - 1), ctx->m + U);
   if (s != OSP_OK) return s;
   return finish_call(ctx, m_before, st);
@@ -495,7 +597,7 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
       ctx->own_stream = e == cudaSuccess;
     }
   }
-  if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 256 * 1024);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, kPinnedBytes);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ingest, cudaFuncAttributeMaxDynamicSharedMemorySize, kIngestSmem);

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   __shared__ int s_bad, s_ndel;
   __shared__ unsigned s_flags[kIngestThreads];
   Ctl* ctl = d.ctl;
+  if (U < 0) U = ctl->batch_U;  // replayed from a CUDA graph: the size is set per call
   const int tid = threadIdx.x;
   const int n_old = ctl->n;
   if (tid == 0) {

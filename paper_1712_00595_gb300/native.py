@@ -37,7 +37,7 @@ EXPORTED = [
 class osp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("max_nodes", C.c_int64), ("push_alpha", C.c_double), ("push_beta", C.c_double),
-                ("max_iter", C.c_int32), ("node_order", C.c_int32)]
+                ("max_iter", C.c_int32), ("node_order", C.c_int32), ("use_graphs", C.c_int32)]
 
 
 class osp_batch_stats(C.Structure):
@@ -141,7 +141,7 @@ class Engine:
     """One engine context (osp_ctx). Methods mirror the C ABI one to one."""
 
     def __init__(self, precision=OSP_PREC_FP32_ACC64, device=0, stream=None, max_nodes=0,
-                 push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0):
+                 push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0, use_graphs=False):
         L = load_library()
         opt = osp_options()
         L.osp_default_options(C.byref(opt))
@@ -153,6 +153,7 @@ class Engine:
         opt.push_beta = push_beta
         opt.max_iter = max_iter
         opt.node_order = node_order
+        opt.use_graphs = int(bool(use_graphs))
         h = C.c_void_p()
         s = L.osp_create(C.byref(h), C.byref(opt))
         if s != OSP_OK:

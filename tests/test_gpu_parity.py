@@ -184,6 +184,56 @@ def test_dense_offset_scan_then_push_steps(prec):
     eng.close()
 
 
+@pytest.mark.parametrize("seeds", [[0], [0, 17, 99, 250]])
+def test_graph_replay_matches_eager_launches(seeds):
+    """The same batches through CUDA-graph replays (several batch-size buckets,
+    a change of eps, a fixed step count) and through eager launches agree with
+    each other and with the oracle."""
+    rng = np.random.default_rng(55)
+    n = 400
+    src, dst = hub_graph(rng, n=n, m=3000, hub_in=300, hub_out=200, mids=5)
+    es = W.EdgeSet(src, dst)
+    dead = np.zeros(n + 10 * 400 + 8, np.uint8)
+    nn = n
+    batches = []
+    for k in (5, 150, 300, 17, 150, 1):
+        ops, nn = W.random_mixed_batch(rng, nn, es, dead, k, protect=tuple(seeds))
+        batches.append(ops)
+    engs = []
+    for graphs in (False, True):
+        e = N.Engine(precision=N.OSP_PREC_FP64, device=0, max_nodes=n + 4096, use_graphs=graphs)
+        e.load_graph(n, src, dst)
+        e.set_seeds(np.array(seeds, np.int32), C_RESTART)
+        e.init_scores(1e-12)
+        engs.append(e)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o = [O.cpi(*cur, s, C_RESTART, 1e-13)[0] for s in seeds]
+    for b, ops in enumerate(batches):
+        eps = 1e-12 if b != 3 else 1e-9
+        if b == 4:
+            for e in engs:
+                e.set_fixed_iterations(6)
+        sts = [e.apply_updates(ops, eps) for e in engs]
+        if b == 4:
+            for e in engs:
+                e.set_fixed_iterations(0)
+        assert sts[0]["iterations"] == sts[1]["iterations"]
+        assert sts[0]["kernel_launches"] == sts[1]["kernel_launches"]
+        assert g.apply(ops, protect=tuple(seeds)) == -1
+        new = g.csr()
+        for j, s in enumerate(seeds):
+            a, c = engs[0].query(j), engs[1].query(j)
+            assert l1(a, c) <= 1e-13
+            if b < 3:  # exact mode until the eps change (later batches keep its truncation)
+                r_o[j], _, _, _ = O.osp(cur, new, r_o[j], C_RESTART, 1e-13)
+                assert l1(c, r_o[j]) <= 1e-10
+        cur = new
+    check_graph(engs[1], g)
+    for e in engs:
+        e.close()
+
+
 def test_invalid_batches_rejected_state_unchanged():
     rng = np.random.default_rng(9)
     n = 50
