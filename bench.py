@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU time bound of the cpu_baseline sample (whole batches)")
+    p.add_argument("--launch", default="graphs", choices=["graphs", "eager"],
+                   help="batch kernels replayed from CUDA graphs, or launched one by one")
     p.add_argument("--workload", default="rmat20", choices=["rmat20"] + sorted(MULTI_WORKLOADS),
                    help="rmat20: the one-seed headline; the others track many seeds at once")
     p.add_argument("--log2n", type=int, default=0,
@@ -102,12 +104,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def alg_bytes(st, n, m, bx, bs):
-    """Algorithmic bytes of one propagation launch (each operand once):
-    pull step  4 m (in-list ids) + n (8 off/len + bx gathered y + bx written y + bs scale + 16 r RMW)
-    push step  4 E_F + (8 + bx) |F| + (bx + 16) |F'|."""
+def alg_bytes(st, n, m, bx, bs, S=1):
+    """Algorithmic bytes of one propagation launch (each operand once), for S
+    seeds, gather vectors of bx bytes and FP64 sums:
+    pull step  4 m (in-list ids) + 4 (|V| + 1) (list starts) + S bx |src| (each
+               source's y once) + S (bx + 16) |V| (write y, read and write r)
+               + 8 S (|x| partials), V = nodes with an in-edge, src = nodes with
+               an out-edge
+    push step  4 E_F + (8 + bx) |F| + (bx + 16) |F'|  (one seed).
+    bs (scale bytes) is not an operand of this count; nodes without in-edges
+    need no r update and are not counted."""
+    del n, bs
     pull_steps = st["iterations"] - st["push_iterations"]
-    pull = pull_steps * (4 * m + n * (8 + 2 * bx + bs + 16))
+    V, src = st["pull_dst_nodes"], st["pull_src_nodes"]
+    pull = pull_steps * (4 * m + 4 * (V + 1) + S * bx * src + S * (bx + 16) * V + 8 * S)
+    if st["push_iterations"] == 0:
+        return pull
     ef = st["visited_edges"] - pull_steps * m
     push = 4 * ef + (8 + bx) * st["push_frontier"] + (bx + 16) * st["push_reached"]
     return pull + push
@@ -320,8 +332,8 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tstream = torch.cuda.Stream(device=dev)
 
-    def new_engine(prec):
-        e = N.Engine(precision=prec, device=local, stream=tstream.cuda_stream)
+    def new_engine(prec, graphs=args.launch == "graphs"):
+        e = N.Engine(precision=prec, device=local, stream=tstream.cuda_stream, use_graphs=graphs)
         e.load_graph(n, src, dst)
         e.set_seeds([seed], C_RESTART)
         e.init_scores(args.eps_init)
@@ -384,7 +396,8 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "batches/s", "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "accumulate": "f64", "data": "synthetic",
-        "config": workload_config(args, n, len(src), seed, "fp32 products, fp64 accumulation"),
+        "config": dict(workload_config(args, n, len(src), seed, "fp32 products, fp64 accumulation"),
+                       launch=args.launch),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(),
                      "kernel": "k_propagate<float>", "peak_kind": peak_kind + " (hbm_gbs copy)",
@@ -419,6 +432,12 @@ def run_ours(args, rank, world):
                           "iterations": float(np.mean([s["iterations"] for s in st_e])),
                           "ms_propagation": sum(s["ms_propagate"] for s in st_e) / K})
         out["eps_sweep"] = sweep
+        # ---- the other launch mode (graph replays vs one launch per kernel) ----
+        e = new_engine(N.OSP_PREC_FP32_ACC64, graphs=args.launch != "graphs")
+        ms_o, _ = run(e, args.eps, Wm)
+        e.close()
+        out["other_launch_mode"] = {"launch": "eager" if args.launch == "graphs" else "graphs",
+                                    "value": K / (sum(ms_o) / 1e3), "unit": "batches/s"}
         # ---- end to end through the host API: host batch in, top of the scores out ----
         e = new_engine(N.OSP_PREC_FP32_ACC64)
         host_ops = [np.ascontiguousarray(s) for s in stream]
@@ -477,13 +496,10 @@ def make_multi_workload(name, log2n):
     return cfg, n, src, dst, seeds, stream, config
 
 
-def multi_alg_bytes(st, n, m, Sp, by):
-    """Algorithmic bytes of one seed-block launch: x(0) pass 4n (stamps) + n Sp b_y
-    (first gather block); each pull step 4m (in-list ids) + 12n (offset, length,
-    scale) + n Sp b_y (each source row gathered once) + n Sp b_y (next gather
-    block) + 16 n Sp (score block read and written)."""
-    steps = st["iterations"]
-    return 4 * n + n * Sp * by + steps * (4 * m + 12 * n + n * Sp * (2 * by + 16))
+def multi_alg_bytes(st, m, S, by):
+    """Algorithmic bytes of one seed-block launch: its pull steps, counted as in
+    alg_bytes for S seeds (the seed block never pushes)."""
+    return alg_bytes(dict(st, push_iterations=0), 0, m, by, 0, S=S)
 
 
 def run_multi(args, rank, world):
@@ -543,9 +559,9 @@ def run_multi(args, rank, world):
     t = dist_max(sum(ms) / 1e3, world)
     value = world * K / t
     prop_ms = sum(s["ms_propagate"] for s in stats)
-    ab = sum(multi_alg_bytes(s, s["n_nodes"], s["m_edges"], Sp, by) for s in stats)
+    ab = sum(multi_alg_bytes(s, s["m_edges"], S, by) for s in stats)
     peak, peak_kind = peaks()
-    step_bytes = 4 * stats[-1]["m_edges"] + 12 * stats[-1]["n_nodes"] + stats[-1]["n_nodes"] * Sp * (2 * by + 16)
+    step_bytes = multi_alg_bytes(dict(stats[-1], iterations=1), stats[-1]["m_edges"], S, by)
     med_step = float(np.median(steps_us[1:])) if len(steps_us) > 1 else float("nan")
     out = {
         "metric": METRIC, "value": value, "unit": "batches/s", "seed_batches_per_s": value * S,

@@ -122,6 +122,8 @@ typedef struct {
     float ms_propagate;      /* device time of the propagation kernel (CUDA events) */
     int32_t kernel_launches; /* kernels this call launched */
     int32_t reserved;
+    int64_t pull_dst_nodes;  /* nodes with a nonempty in-list (destinations of a pull step) */
+    int64_t pull_src_nodes;  /* nodes with a nonempty out-list (sources a pull step gathers) */
 } osp_batch_stats;
 
 /* Fill *opt with defaults (FP32_ACC64, device 0, engine-owned stream). */

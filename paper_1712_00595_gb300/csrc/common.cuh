@@ -55,6 +55,7 @@ struct Ctl {
   int n_opieces;               // several seeds: offset items (256 entries of a changed row)
   int hub_thr, hub_piece;      // pull step: in-lists longer than hub_thr go in pieces of hub_piece
   int batch_U;                 // ops of the batch, for a k_ingest replayed from a CUDA graph
+  long long n_dst_nz, n_src_nz;  // nodes with a nonempty in-list / out-list (pull plan)
   int epoch;                   // frontier mark of x(0); step i uses epoch + i
   int q_size[2];               // frontier queue lengths
   unsigned int bar_count, bar_gen;

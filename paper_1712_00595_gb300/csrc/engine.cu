@@ -327,6 +327,8 @@ void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_befor
   st->kernel_launches = ctx->launches;
   st->push_frontier = h.push_f;
   st->push_reached = h.push_r;
+  st->pull_dst_nodes = h.n_dst_nz;
+  st->pull_src_nodes = h.n_src_nz;
   float a = 0.f, b = 0.f;
   if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st->ms_update = a;
   if (cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess) st->ms_propagate = b;

@@ -166,6 +166,8 @@ __global__ void k_reset_batch(Dev d) {
   c->q_size[0] = 0;
   c->q_size[1] = 0;
   c->dense0 = 0;
+  c->n_dst_nz = 0;
+  c->n_src_nz = 0;
   for (int i = 0; i < 4; ++i) c->ctr[i] = 0;
   c->bar_count = 0;
   c->iter = 0;

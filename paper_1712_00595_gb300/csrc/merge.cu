@@ -345,10 +345,26 @@ __global__ void k_pull_plan(Dev d, int hub_thr, int node_w) {
     d.task_first[t] = t == nt ? n : lo;
   }
   const int lane = threadIdx.x & 31;
+  __shared__ unsigned long long s_cnt[2];
+  if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0;
+  __syncthreads();
+  unsigned nd = 0, ns = 0;  // destinations and sources of the pull steps (byte accounting)
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += nth) {
     const int v = base + lane;
-    const bool h = v < n && d.len_c[v] > hub_thr;
+    const int lc = v < n ? d.len_c[v] : 0;
+    const bool h = lc > hub_thr;
     warp_append(h, v, d.hubs, &ctl->n_hubs);
+    nd += __popc(__ballot_sync(0xffffffffu, lc > 0));
+    ns += __popc(__ballot_sync(0xffffffffu, v < n && d.len_r[v] > 0));
+  }
+  if (lane == 0) {
+    atomicAdd(&s_cnt[0], (unsigned long long)nd);
+    atomicAdd(&s_cnt[1], (unsigned long long)ns);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd((unsigned long long*)&ctl->n_dst_nz, s_cnt[0]);
+    if (s_cnt[1]) atomicAdd((unsigned long long*)&ctl->n_src_nz, s_cnt[1]);
   }
 }
 

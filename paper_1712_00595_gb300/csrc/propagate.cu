@@ -235,14 +235,14 @@ __device__ void push_big_rows(const Dev& d, int nb, int* qdst, int* qdst_size, i
 __device__ __forceinline__ void finish_node(const Dev& d, int v, double x, void* yd, bool fp32,
                                             double& l1) {
   if (!OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "finish node", v, 0, 0)) return;
-  d.r[v] += x;
+  if (x != 0.0) d.r[v] += x;  // an empty in-list leaves r as it is
   l1 += fabs(x);
   if (fp32) ((float*)yd)[v] = (float)x * __ldg(d.scale_f + v);
   else ((double*)yd)[v] = x * __ldg(d.scale_d + v);
 }
 
 // Dense step. Warp tasks of about kTaskItems edges + nodes (planned per batch,
-// lists never split) are dealt round-robin to the warps; a task is walked 32
+// lists never split) are taken from a shared counter; a task is walked 32
 // consecutive nodes at a time. The short in-lists of such a chunk are summed as
 // one flattened, coalesced stream of edges (segmented warp scan, four rounds
 // of 32 edges with their loads in flight), a longer list by the whole warp

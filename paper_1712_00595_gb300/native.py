@@ -48,7 +48,8 @@ class osp_batch_stats(C.Structure):
                 ("changed_rows", C.c_int64), ("bad_op", C.c_int64),
                 ("push_frontier", C.c_int64), ("push_reached", C.c_int64),
                 ("ms_update", C.c_float), ("ms_propagate", C.c_float),
-                ("kernel_launches", C.c_int32), ("reserved", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("reserved", C.c_int32),
+                ("pull_dst_nodes", C.c_int64), ("pull_src_nodes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -11,11 +11,18 @@ import bench
 
 def test_alg_bytes_pull_and_push():
     st = {"iterations": 3, "push_iterations": 1, "visited_edges": 100 + 2 * 1000,
-          "push_frontier": 10, "push_reached": 40}
+          "push_frontier": 10, "push_reached": 40, "pull_dst_nodes": 30, "pull_src_nodes": 35}
     n, m = 50, 1000
-    pull = 2 * (4 * m + n * (8 + 8 + 4 + 16))
+    pull = 2 * (4 * m + 4 * 31 + 4 * 35 + 20 * 30 + 8)
     push = 4 * 100 + 12 * 10 + 20 * 40
     assert bench.alg_bytes(st, n, m, 4, 4) == pull + push
+
+
+def test_alg_bytes_seed_block():
+    st = {"iterations": 2, "pull_dst_nodes": 30, "pull_src_nodes": 35}
+    m, S = 1000, 64
+    step = 4 * m + 4 * 31 + S * 2 * 35 + S * (2 + 16) * 30 + 8 * S
+    assert bench.multi_alg_bytes(st, m, S, 2) == 2 * step
 
 
 def _free_port():
