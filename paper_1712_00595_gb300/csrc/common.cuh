@@ -29,7 +29,10 @@ constexpr int kHubThreshold = 1024;  // pull step: in-lists longer than this are
 constexpr int kHubPiece = 1024;      // pull step: edges per hub piece
 constexpr int kMultiHub = 256;       // seed block: in-lists longer than this, in pieces of this size
 constexpr int kMultiNodeItems = 4;   // seed block: task items per node (a node's score row costs more)
-constexpr int kTaskItems = 1024;     // pull step: items (edges + nodes) per warp task
+#ifndef OSP_TASK_ITEMS
+#define OSP_TASK_ITEMS 1024
+#endif
+constexpr int kTaskItems = OSP_TASK_ITEMS;  // pull step: items (edges + nodes) per warp task
 constexpr double kPushAlpha = 14.0;  // push step while frontier out-edges <= m / alpha
 constexpr double kPushBeta = 24.0;   // ... and frontier size <= n / beta
 

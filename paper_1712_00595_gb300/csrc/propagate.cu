@@ -373,28 +373,55 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
         }
       }
       T s = wacc[lane];
-      // longer lists: the whole warp, eight coalesced loads and gathers in flight per lane
+      // longer lists: the whole warp, blocks of 256 entries (eight coalesced id
+      // loads and gathers per lane); the ids of the next block (of this list or
+      // the next one) load while the current block's gathers are in flight
       unsigned hm = __ballot_sync(0xffffffffu, !light && !hub);
-      while (hm) {
-        const int l = __ffs(hm) - 1;
+      if (hm) {
+        int l = __ffs(hm) - 1;
         hm &= hm - 1;
         const int* p = d.pool_c + __shfl_sync(0xffffffffu, o, l);
-        const int hl = __shfl_sync(0xffffffffu, len, l);
-        T acc = (T)0;
-        for (int jb = 0; jb < hl; jb += 256) {
-          int a[8];
+        int hl = __shfl_sync(0xffffffffu, len, l);
+        int jb = 0;
+        int a[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int j = jb + 32 * q + lane;
-            a[q] = j < hl ? __ldg(p + j) : -1;
-          }
+        for (int q = 0; q < 8; ++q) a[q] = 32 * q + lane < hl ? __ldg(p + 32 * q + lane) : -1;
+        T acc = (T)0;
+        for (;;) {
           T t[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) t[q] = a[q] >= 0 ? ys[a[q]] : (T)0;
+          // the next block: the rest of this list, else the next long list
+          const bool same = jb + 256 < hl;
+          int nl = l, nhl = hl, njb = jb + 256;
+          const int* np = p;
+          if (!same && hm) {
+            nl = __ffs(hm) - 1;
+            nhl = __shfl_sync(0xffffffffu, len, nl);
+            np = d.pool_c + __shfl_sync(0xffffffffu, o, nl);
+            njb = 0;
+          }
+          const bool more = same || hm != 0;
+          if (more) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int j = njb + 32 * q + lane;
+              a[q] = j < nhl ? __ldg(np + j) : -1;
+            }
+          }
           acc += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+          if (!same) {  // list l is complete
+            const T tot = warp_sum(acc);
+            if (lane == l) s = tot;
+            acc = (T)0;
+            if (!hm) break;
+            hm &= hm - 1;
+          }
+          l = nl;
+          hl = nhl;
+          p = np;
+          jb = njb;
         }
-        acc = warp_sum(acc);
-        if (lane == l) s = acc;
       }
       if (valid && !hub) finish_node(d, v, (double)s, yd, kF32, l1);
     }
