@@ -101,6 +101,10 @@ typedef struct {
                            graphs (one pair per batch-size bucket, eps and fixed step counts,
                            captured on first use and rebuilt when device buffers move),
                            which removes most host launch work per batch. */
+    int32_t autotune;   /* != 0: osp_init_scores first times the pull-step schedule candidates
+                           (task size 512/1024/2048 x long-list threshold, and node weight
+                           2/4/8 with several seeds) on the first CPI steps and keeps the
+                           fastest for every later call (osp_get_schedule reports it). */
 } osp_options;
 
 /* Per-call statistics (the columns of Table 2 plus bookkeeping). */
@@ -239,6 +243,11 @@ osp_status osp_get_size(osp_ctx *ctx, int64_t *n, int64_t *m);
  * and ||x(k)||_1 at its stop. *count = min(S, cap). */
 osp_status osp_get_seed_stats(osp_ctx *ctx, int32_t *iterations, double *qoff_l1,
                               double *last_l1, int32_t cap, int32_t *count);
+
+/* The pull-step schedule in force (host array of 4): items per warp task,
+ * in-list length above which lists are summed in pieces, the piece length, and
+ * the items a node counts for in task planning. */
+osp_status osp_get_schedule(osp_ctx *ctx, int32_t *out);
 
 /* Fix each seed's number of propagation steps for the following init/apply
  * calls (k[j] > 0: seed j runs exactly k[j] steps; 0: its eps rule), to

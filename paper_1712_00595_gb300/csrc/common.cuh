@@ -29,10 +29,8 @@ constexpr int kHubThreshold = 1024;  // pull step: in-lists longer than this are
 constexpr int kHubPiece = 1024;      // pull step: edges per hub piece
 constexpr int kMultiHub = 256;       // seed block: in-lists longer than this, in pieces of this size
 constexpr int kMultiNodeItems = 4;   // seed block: task items per node (a node's score row costs more)
-#ifndef OSP_TASK_ITEMS
-#define OSP_TASK_ITEMS 1024
-#endif
-constexpr int kTaskItems = OSP_TASK_ITEMS;  // pull step: items (edges + nodes) per warp task
+constexpr int kTaskItems = 1024;     // pull step: default items (edges + nodes) per warp task
+constexpr int kMinTaskItems = 256;   // smallest task size a schedule may choose (sizes the plan)
 constexpr double kPushAlpha = 14.0;  // push step while frontier out-edges <= m / alpha
 constexpr double kPushBeta = 24.0;   // ... and frontier size <= n / beta
 
@@ -130,7 +128,7 @@ struct Dev {
   // kTaskItems items (edges + nodes, lists never split), and the long in-lists
   // summed in pieces
   unsigned* pc;                       // [nc + 1]  pc[v] = sum of in-list lengths below v
-  int* task_first;                    // [(nc + pool cap) / kTaskItems + 2] first node of each warp task
+  int* task_first;                    // [(kMultiNodeItems nc + pool cap) / kMinTaskItems + 2] first node of each warp task
   int* hubs; int* hub_pstart; double* hub_acc; int* hub_cnt;  // [pool cap / kHubThreshold + 2]
   int* big_u; double* big_y;  // push step: rows longer than kHubThreshold [pool cap / kHubThreshold + 2]
   // reductions and history

@@ -1,6 +1,7 @@
 // Host engine behind the C ABI of include/osp.h: device memory, the graph
 // loader, the per-batch launch sequence and the queries.
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -49,6 +50,9 @@ struct osp_ctx {
   int grid_multi = 0;
   int grid_multi_init = 0;
   int seed_force_max = 0;      // largest per-seed step count set by osp_set_seed_iterations
+  // pull-step schedule: task size, long-list threshold and piece, node weight
+  // (defaults by seed count until osp_init_scores autotunes them)
+  int sched[4] = {0, 0, 0, 0};
   // CUDA graphs of the batch path, by (ingest shared-memory bucket, eps, fixed
   // step counts); dropped whenever device buffers move
   struct GraphPair {
@@ -361,6 +365,15 @@ osp_status finish_call(osp_ctx* ctx, int64_t m_before, osp_batch_stats* st) {
   return OSP_OK;
 }
 
+// The pull-step schedule in force: {task items, long-list threshold, piece,
+// node weight}; unset entries take the defaults of the seed count.
+const int* schedule(osp_ctx* ctx) {
+  static const int single[4] = {kTaskItems, kHubThreshold, kHubPiece, 1};
+  static const int multi[4] = {kTaskItems, kMultiHub, kMultiHub, kMultiNodeItems};
+  if (ctx->sched[0] > 0) return ctx->sched;
+  return ctx->S > 1 ? multi : single;
+}
+
 // Pull-step plan for the graph as it is after the merge: in-list length prefix
 // over the first n_bound + 1 ids (ids at or above n have empty lists) and the
 // merge-path tile starts.
@@ -377,11 +390,10 @@ osp_status plan_pull(osp_ctx* ctx, int64_t n_bound, int64_t m_bound) {
   ++ctx->launches;
   k_scan_add<<<(ns + 255) / 256, 256, 0, st>>>(ctx->d.pc, ctx->scan_bsum, ns);
   ++ctx->launches;
-  const bool multi = ctx->S > 1;
-  k_pull_plan<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d, multi ? kMultiHub : kHubThreshold,
-                                                 multi ? kMultiNodeItems : 1);
+  const int* sc = schedule(ctx);
+  k_pull_plan<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d, sc[1], sc[3], sc[0]);
   ++ctx->launches;
-  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d, multi ? kMultiHub : kHubPiece);
+  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d, sc[2]);
   ++ctx->launches;
   CK(cudaGetLastError());
   return OSP_OK;
@@ -770,7 +782,7 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
     AL(d.piece_base, npc, 0);
   }
   AL(d.pc, nc + 1, 0);
-  AL(d.task_first, (int64_t)(kMultiNodeItems * nc + (int64_t)cap) / kTaskItems + 2, 0);
+  AL(d.task_first, (int64_t)(kMultiNodeItems * nc + (int64_t)cap) / kMinTaskItems + 2, 0);
   {
     // lists longer than a threshold t number at most (live edges) / t <= cap / t;
     // the pull plan uses t = kMultiHub for the seed block, kHubThreshold otherwise
@@ -924,12 +936,8 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
   return OSP_OK;
 }
 
-osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
-  osp_status s = check_ready(ctx, false);
-  if (s != OSP_OK) return s;
-  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
-  ctx->launches = 0;
-  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+// x(0) = c e_s per seed, with the scores cleared.
+osp_status enqueue_cpi_start(osp_ctx* ctx) {
   k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
   ++ctx->launches;
   if (ctx->S > 1) {
@@ -942,6 +950,73 @@ osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
   }
   ++ctx->launches;
   CK(cudaGetLastError());
+  return OSP_OK;
+}
+
+// Time the first CPI steps under each candidate pull schedule and keep the
+// fastest: three steps with several seeds (every step is a pull step), twelve
+// with one (the first steps from a single seed are push steps).
+osp_status autotune(osp_ctx* ctx, double eps) {
+  const bool multi = ctx->S > 1;
+  const int tis[3] = {512, 1024, 2048};
+  const int hubs_single[3] = {512, 1024, 4096};
+  const int hubs_multi[3] = {kMultiHub, 2 * kMultiHub, 4 * kMultiHub};
+  const int nws_multi[3] = {2, 4, 8};
+  std::vector<std::array<int, 4>> cands;
+  for (int ti : tis)
+    for (int h = 0; h < 3; ++h)
+      for (int w = 0; w < (multi ? 3 : 1); ++w) {
+        const int hub = multi ? hubs_multi[h] : hubs_single[h];
+        cands.push_back({ti, hub, hub, multi ? nws_multi[w] : 1});
+      }
+  PropParams pp = prop_params(ctx, eps);
+  pp.force_iters = multi ? 3 : 12;
+  pp.max_iter = std::max(pp.max_iter, pp.force_iters);
+  float best = 1e30f;
+  std::array<int, 4> pick = cands[0];
+  for (int trial = -1; trial < (int)cands.size(); ++trial) {  // trial -1 warms up
+    const auto& cd = cands[trial < 0 ? 0 : trial];
+    for (int i = 0; i < 4; ++i) ctx->sched[i] = cd[i];
+    osp_status s = enqueue_cpi_start(ctx);
+    if (s == OSP_OK) s = plan_pull(ctx, ctx->n, ctx->m);
+    if (s != OSP_OK) return s;
+    CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    s = enqueue_propagate(ctx, pp, true);
+    if (s != OSP_OK) return s;
+    CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev[2]));
+    Ctl h;
+    s = read_ctl(ctx, &h);
+    if (s != OSP_OK) return s;
+    if (h.status != 0) {
+      ctx->broken = true;
+      return fail(ctx, (osp_status)h.status, "device error while tuning the pull schedule");
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]));
+    if (trial >= 0 && ms < best) {
+      best = ms;
+      pick = cd;
+    }
+  }
+  for (int i = 0; i < 4; ++i) ctx->sched[i] = pick[i];
+  drop_graphs(ctx);  // captured plans hold the previous schedule
+  return OSP_OK;
+}
+
+osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
+  osp_status s = check_ready(ctx, false);
+  if (s != OSP_OK) return s;
+  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  ctx->launches = 0;
+  if (ctx->opt.autotune) {
+    s = autotune(ctx, eps);
+    if (s != OSP_OK) return s;
+    ctx->launches = 0;
+  }
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  s = enqueue_cpi_start(ctx);
+  if (s != OSP_OK) return s;
   s = run_propagation(ctx, eps, ctx->n, ctx->m, true);
   if (s != OSP_OK) return s;
   s = finish_call(ctx, ctx->m, stats);
@@ -1138,6 +1213,13 @@ osp_status osp_get_seed_stats(osp_ctx* ctx, int32_t* iterations, double* qoff_l1
   }
   CK(cudaStreamSynchronize(st));
   *count = k;
+  return OSP_OK;
+}
+
+osp_status osp_get_schedule(osp_ctx* ctx, int32_t* out) {
+  if (!ctx || !out) return OSP_EINVAL;
+  const int* sc = schedule(ctx);
+  for (int i = 0; i < 4; ++i) out[i] = sc[i];
   return OSP_OK;
 }
 

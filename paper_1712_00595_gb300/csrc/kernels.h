@@ -13,7 +13,7 @@ __global__ void k_merge_count(Dev d);
 __global__ void k_merge_plan(Dev d);
 __global__ void k_merge_write(Dev d);
 __global__ void k_merge_finish(Dev d);
-__global__ void k_pull_plan(Dev d, int hub_thr, int node_w);
+__global__ void k_pull_plan(Dev d, int hub_thr, int node_w, int task_items);
 __global__ void k_hub_prefix(Dev d, int hub_piece);
 __global__ void k_set_scale(Dev d, int n, double c);
 __global__ void k_scan_local(const int* __restrict__ len, unsigned* out, unsigned* bsum, int n);

@@ -319,15 +319,15 @@ __global__ void k_merge_finish(Dev d) {
 }
 
 // Pull-step plan, part 1: warp task t starts at the first node v with
-// pc[v] + node_w v >= t * kTaskItems (so a task holds about kTaskItems items,
+// pc[v] + node_w v >= t * task_items (so a task holds about task_items items,
 // an edge counting 1 and a node node_w, and never splits a list); in-lists
 // longer than hub_thr are listed for piecewise summation.
-__global__ void k_pull_plan(Dev d, int hub_thr, int node_w) {
+__global__ void k_pull_plan(Dev d, int hub_thr, int node_w, int task_items) {
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   const int n = ctl->n;
   const long long W = (long long)node_w * n + ctl->m;
-  const int nt = (int)((W + kTaskItems - 1) / kTaskItems);
+  const int nt = (int)((W + task_items - 1) / task_items);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   if (tid == 0) {
@@ -335,7 +335,7 @@ __global__ void k_pull_plan(Dev d, int hub_thr, int node_w) {
     ctl->hub_thr = hub_thr;
   }
   for (int t = tid; t <= nt; t += nth) {
-    const long long target = (long long)t * kTaskItems;
+    const long long target = (long long)t * task_items;
     int lo = 0, hi = n;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;

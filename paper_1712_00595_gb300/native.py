@@ -30,14 +30,15 @@ EXPORTED = [
     "osp_query", "osp_query_device", "osp_topk", "osp_export_graph", "osp_get_size",
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
     "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
-    "osp_set_seed_iterations",
+    "osp_set_seed_iterations", "osp_get_schedule",
 ]
 
 
 class osp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("max_nodes", C.c_int64), ("push_alpha", C.c_double), ("push_beta", C.c_double),
-                ("max_iter", C.c_int32), ("node_order", C.c_int32), ("use_graphs", C.c_int32)]
+                ("max_iter", C.c_int32), ("node_order", C.c_int32), ("use_graphs", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class osp_batch_stats(C.Structure):
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
             "osp_topk_noalloc": (C.c_int, [P, i64, i32, C.c_int, P, P, P, P]),
             "osp_get_seed_stats": (C.c_int, [P, P, P, P, i32, P]),
             "osp_set_seed_iterations": (C.c_int, [P, P, i32]),
+            "osp_get_schedule": (C.c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -142,7 +144,8 @@ class Engine:
     """One engine context (osp_ctx). Methods mirror the C ABI one to one."""
 
     def __init__(self, precision=OSP_PREC_FP32_ACC64, device=0, stream=None, max_nodes=0,
-                 push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0, use_graphs=False):
+                 push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0, use_graphs=False,
+                 autotune=False):
         L = load_library()
         opt = osp_options()
         L.osp_default_options(C.byref(opt))
@@ -155,6 +158,7 @@ class Engine:
         opt.max_iter = max_iter
         opt.node_order = node_order
         opt.use_graphs = int(bool(use_graphs))
+        opt.autotune = int(bool(autotune))
         h = C.c_void_p()
         s = L.osp_create(C.byref(h), C.byref(opt))
         if s != OSP_OK:
@@ -253,6 +257,12 @@ class Engine:
             return self._check(self._L.osp_set_seed_iterations(self._h, None, 0))
         k = np.ascontiguousarray(k, np.int32)
         return self._check(self._L.osp_set_seed_iterations(self._h, _ptr(k), int(k.size)))
+
+    def get_schedule(self):
+        """(task items, long-list threshold, piece length, node items) in force."""
+        out = np.zeros(4, np.int32)
+        self._check(self._L.osp_get_schedule(self._h, _ptr(out)))
+        return tuple(int(x) for x in out)
 
     def get_seed_stats(self, cap=256):
         """Per seed of the last call: (steps run, ||x(0)||_1, ||x(k)||_1 at its stop)."""

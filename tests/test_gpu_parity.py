@@ -234,6 +234,30 @@ def test_graph_replay_matches_eager_launches(seeds):
         e.close()
 
 
+@pytest.mark.parametrize("seeds", [[0], [0, 17, 99]])
+def test_autotuned_schedule_gives_the_same_scores(seeds):
+    rng = np.random.default_rng(66)
+    n = 3000
+    src, dst = hub_graph(rng, n=n, m=30000, hub_in=2500, hub_out=900, mids=12)
+    stream = W.edge_update_stream(src, dst, n, 3, 60, 40, seed=9)
+    out = []
+    for tune in (False, True):
+        e = N.Engine(precision=N.OSP_PREC_FP64, device=0, autotune=tune, use_graphs=tune)
+        e.load_graph(n, src, dst)
+        e.set_seeds(np.array(seeds, np.int32), C_RESTART)
+        e.init_scores(1e-12)
+        for ops in stream:
+            e.apply_updates(ops, 1e-12)
+        out.append(([e.query(j) for j in range(len(seeds))], e.get_schedule()))
+        e.close()
+    ti, thr, piece, nw = out[1][1]
+    assert ti in (512, 1024, 2048) and thr == piece
+    assert thr in ((256, 512, 1024) if len(seeds) > 1 else (512, 1024, 4096))
+    assert nw in ((2, 4, 8) if len(seeds) > 1 else (1,))
+    for a, b in zip(out[0][0], out[1][0]):
+        assert l1(a, b) <= 1e-12
+
+
 def test_invalid_batches_rejected_state_unchanged():
     rng = np.random.default_rng(9)
     n = 50
