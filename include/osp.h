@@ -230,6 +230,25 @@ osp_status osp_topk_noalloc(const double *scores_device, int64_t n, int32_t k, i
                             int32_t *ids_device, double *out_scores_device,
                             int32_t *k_out_device, void *stream);
 
+/* Query slots for serving: queries that overlap on the device with the next
+ * update batch. Allocates nslots (0 <= nslots <= 64; 0 frees them) slots, each
+ * with its own top-k scratch and an n-double column buffer (about 8 bytes per
+ * node slot plus 150 KB, so the HBM budget for queries sets nslots), and a
+ * second CUDA stream for them. A query enqueued with osp_topk_async reads the
+ * scores as of the last completed init/apply call; the ingest, merge and
+ * offset kernels of the next apply run alongside it, and that call's
+ * propagation kernel (the only kernel that changes the scores) waits for
+ * every query enqueued before it. */
+osp_status osp_query_slots(osp_ctx *ctx, int32_t nslots);
+
+/* Enqueue the top-k of seed seed_idx (as osp_topk) in a free slot and return
+ * without waiting. OSP_ESTATE if the slot still holds a query. */
+osp_status osp_topk_async(osp_ctx *ctx, int32_t slot, int32_t seed_idx, int32_t k, int normalize);
+
+/* Wait for the slot's query and copy its result (host arrays of k entries,
+ * count in *k_out); the slot is free again afterwards. */
+osp_status osp_topk_wait(osp_ctx *ctx, int32_t slot, int32_t *ids, double *scores, int32_t *k_out);
+
 /* Copy the current graph as sorted adjacency (host arrays): direction 0 gives
  * out-edges (CSR of A~'s pattern), 1 gives in-edges (CSC). ptr has n+1 entries,
  * idx has m; each list ascending. */

@@ -29,6 +29,32 @@ struct HostCtlView {  // the leading fields of Ctl, read back after every call
   Ctl c;
 };
 
+constexpr int kMaxQuerySlots = 64;
+
+// Device scratch of one top-k query.
+struct TopkScratch {
+  TopkState* st;
+  unsigned* hist;
+  int* blk_a;
+  int* blk_b;
+  unsigned long long* keys;
+  int* ids;
+  int* out_ids;
+  double* out_sc;
+  int* out_k;
+  double* dsum;
+};
+
+// A query slot: its own scratch and column buffer, so that queries in flight on
+// the query stream do not share memory with each other or with the engine.
+struct QuerySlot {
+  TopkScratch t{};
+  double* col = nullptr;
+  cudaEvent_t done = nullptr;
+  int busy = 0;
+  int k = 0;
+};
+
 }  // namespace
 
 struct osp_ctx {
@@ -60,6 +86,12 @@ struct osp_ctx {
     int launches = 0;
   };
   std::map<std::tuple<int, double, int, int>, GraphPair> graphs;
+  // query slots (osp_query_slots): queries run on qstream after the scores of
+  // ev_scores; the next propagation waits for ev_queries
+  std::vector<QuerySlot> qslots;
+  std::vector<void*> qallocs;
+  cudaStream_t qstream = nullptr;
+  cudaEvent_t ev_scores = nullptr, ev_queries = nullptr;
   std::vector<void*> mallocs;  // buffers of the seed block, freed when the seeds change
   int fixed_iters = 0;
   int grid_prop = 0;
@@ -132,6 +164,15 @@ void drop_graphs(osp_ctx* ctx) {
   ctx->graphs.clear();
 }
 
+void free_slots(osp_ctx* ctx) {
+  if (ctx->qstream) cudaStreamSynchronize(ctx->qstream);
+  for (auto& q : ctx->qslots)
+    if (q.done) cudaEventDestroy(q.done);
+  ctx->qslots.clear();
+  for (void* p : ctx->qallocs) cudaFree(p);
+  ctx->qallocs.clear();
+}
+
 void free_multi(osp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graphs(ctx);
@@ -143,6 +184,7 @@ void free_multi(osp_ctx* ctx) {
 }
 
 void free_all(osp_ctx* ctx) {
+  free_slots(ctx);
   free_multi(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
@@ -435,10 +477,13 @@ osp_status run_propagation(osp_ctx* ctx, double eps, int64_t n_bound, int64_t m_
   const PropParams pp = prop_params(ctx, eps);
   osp_status s = plan_pull(ctx, n_bound, m_bound);
   if (s != OSP_OK) return s;
+  // queries in flight read the scores this kernel changes
+  if (!ctx->qslots.empty()) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_queries, 0));
   CK(cudaEventRecord(ctx->ev[1], ctx->stream));
   s = enqueue_propagate(ctx, pp, init);
   if (s != OSP_OK) return s;
   CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+  if (!ctx->qslots.empty()) CK(cudaEventRecord(ctx->ev_scores, ctx->stream));
   return OSP_OK;
 }
 
@@ -545,9 +590,11 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
     }
     CK(cudaEventRecord(ctx->ev[0], ctx->stream));
     CK(cudaGraphLaunch(it->second.update, ctx->stream));
+    if (!ctx->qslots.empty()) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_queries, 0));
     CK(cudaEventRecord(ctx->ev[1], ctx->stream));
     CK(cudaGraphLaunch(it->second.propagate, ctx->stream));
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    if (!ctx->qslots.empty()) CK(cudaEventRecord(ctx->ev_scores, ctx->stream));
     ctx->launches = it->second.launches;
     return finish_call(ctx, m_before, st);
   }
@@ -557,6 +604,52 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
   s = run_propagation(ctx, eps, std::min<int64_t>(ctx->n + U, ctx->nc - 1), ctx->m + U);
   if (s != OSP_OK) return s;
   return finish_call(ctx, m_before, st);
+}
+
+// Column col of the scores in caller order into dst, on stream st.
+osp_status enqueue_gather(osp_ctx* ctx, cudaStream_t st, int col, double* dst) {
+  const int n = (int)ctx->n;
+  if (ctx->S > 1)
+    k_gather_col<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.mu.r, ctx->d.mu.Sp, col, ctx->d.ext2int, n, dst);
+  else
+    k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dst);
+  ++ctx->launches;
+  CK(cudaGetLastError());
+  return OSP_OK;
+}
+
+// Top-k of rs[0 .. n) on stream st with scratch t: radix select, ordered
+// compaction, one-CTA sort (results in t.out_*).
+osp_status enqueue_topk(osp_ctx* ctx, cudaStream_t st, const double* rs, int n, int k,
+                        int normalize, const TopkScratch& t) {
+  const int g = ctx->num_sms * 4;
+  k_topk_reset<<<1, 1024, 0, st>>>(t.st, t.hist, k);
+  ++ctx->launches;
+  const int widths[6] = {12, 12, 12, 12, 12, 4};
+  for (int w : widths) {
+    k_topk_hist<<<g, 256, 0, st>>>(rs, n, t.st, t.hist, w);
+    ++ctx->launches;
+    k_topk_select<<<1, 1024, 0, st>>>(t.st, t.hist, w, kTopkCand);
+    ++ctx->launches;
+  }
+  const int nb = (n + kTopkChunk - 1) / kTopkChunk;
+  k_topk_count<<<nb, 1024, 0, st>>>(rs, n, t.st, t.blk_a, t.blk_b);
+  ++ctx->launches;
+  k_topk_scan<<<1, 32, 0, st>>>(t.st, t.blk_a, t.blk_b, nb, kTopkCand);
+  ++ctx->launches;
+  k_topk_emit<<<nb, 1024, 0, st>>>(rs, n, t.st, t.blk_a, t.blk_b, t.keys, t.ids);
+  ++ctx->launches;
+  if (normalize) {
+    CK(cudaMemsetAsync(t.dsum, 0, sizeof(double), st));
+    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(rs, n, t.dsum);
+    ++ctx->launches;
+  }
+  const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
+  k_topk_sort<<<1, 1024, smem, st>>>(rs, t.st, t.keys, t.ids, kTopkMaxK + kTopkCand, k,
+                                     normalize ? t.dsum : nullptr, t.out_ids, t.out_sc, t.out_k);
+  ++ctx->launches;
+  CK(cudaGetLastError());
+  return OSP_OK;
 }
 
 }  // namespace
@@ -643,6 +736,9 @@ void osp_destroy(osp_ctx* ctx) {
   for (cudaEvent_t ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->qstream) cudaStreamDestroy(ctx->qstream);
+  if (ctx->ev_scores) cudaEventDestroy(ctx->ev_scores);
+  if (ctx->ev_queries) cudaEventDestroy(ctx->ev_queries);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -864,6 +960,7 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     CK(cudaMemcpy(&dead, ctx->d.dead + s_int[i], 1, cudaMemcpyDeviceToHost));
     if (dead) return fail(ctx, OSP_EINVAL, "seed is a deleted node");
   }
+  if (ctx->qstream) CK(cudaStreamSynchronize(ctx->qstream));  // no query reads the old scores
   free_multi(ctx);
   ctx->seeded = ctx->scored = false;
   Ctl h;
@@ -1014,6 +1111,7 @@ osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
     if (s != OSP_OK) return s;
     ctx->launches = 0;
   }
+  if (!ctx->qslots.empty()) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_queries, 0));
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
   s = enqueue_cpi_start(ctx);
   if (s != OSP_OK) return s;
@@ -1094,45 +1192,100 @@ osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, in
   if (s != OSP_OK) return s;
   if (seed_idx < 0 || seed_idx >= ctx->S || k <= 0 || k > kTopkMaxK || !ids || !scores || !k_out)
     return fail(ctx, OSP_EINVAL, "bad seed index, k outside [1, 4096] or null output");
-  const int n = (int)ctx->n;
-  const int g = ctx->num_sms * 4;
   cudaStream_t st = ctx->stream;
   // rank the scores in caller order, so that ties go to the smaller caller id
-  s = scores_in_caller_order(ctx, seed_idx, 0, ctx->dtmp);
+  s = enqueue_gather(ctx, st, seed_idx, ctx->dtmp);
   if (s != OSP_OK) return s;
-  const double* rs = ctx->dtmp;
-  k_topk_reset<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, k);
-  ++ctx->launches;
-  const int widths[6] = {12, 12, 12, 12, 12, 4};
-  for (int w : widths) {
-    k_topk_hist<<<g, 256, 0, st>>>(rs, n, ctx->tk_state, ctx->tk_hist, w);
-    ++ctx->launches;
-    k_topk_select<<<1, 1024, 0, st>>>(ctx->tk_state, ctx->tk_hist, w, kTopkCand);
-    ++ctx->launches;
-  }
-  const int nb = (n + kTopkChunk - 1) / kTopkChunk;
-  k_topk_count<<<nb, 1024, 0, st>>>(rs, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b);
-  ++ctx->launches;
-  k_topk_scan<<<1, 32, 0, st>>>(ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b, nb, kTopkCand);
-  ++ctx->launches;
-  k_topk_emit<<<nb, 1024, 0, st>>>(rs, n, ctx->tk_state, ctx->tk_blk_a, ctx->tk_blk_b,
-                                   ctx->tk_keys, ctx->tk_ids);
-  ++ctx->launches;
-  if (normalize) {
-    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), st));
-    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(rs, n, ctx->dsum);
-    ++ctx->launches;
-  }
-  const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
-  k_topk_sort<<<1, 1024, smem, st>>>(rs, ctx->tk_state, ctx->tk_keys, ctx->tk_ids,
-                                     kTopkMaxK + kTopkCand, k, normalize ? ctx->dsum : nullptr,
-                                     ctx->tk_out_ids, ctx->tk_out_sc, ctx->tk_out_k);
-  ++ctx->launches;
-  CK(cudaGetLastError());
+  const TopkScratch t{ctx->tk_state, ctx->tk_hist, ctx->tk_blk_a, ctx->tk_blk_b, ctx->tk_keys,
+                      ctx->tk_ids, ctx->tk_out_ids, ctx->tk_out_sc, ctx->tk_out_k, ctx->dsum};
+  s = enqueue_topk(ctx, st, ctx->dtmp, (int)ctx->n, k, normalize, t);
+  if (s != OSP_OK) return s;
   CK(cudaMemcpyAsync(k_out, ctx->tk_out_k, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ids, ctx->tk_out_ids, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(scores, ctx->tk_out_sc, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  return OSP_OK;
+}
+
+osp_status osp_query_slots(osp_ctx* ctx, int32_t nslots) {
+  if (!ctx) return OSP_EINVAL;
+  if (!ctx->loaded) return fail(ctx, OSP_ESTATE, "no graph loaded");
+  if (nslots < 0 || nslots > kMaxQuerySlots) return fail(ctx, OSP_EINVAL, "slots outside [0, 64]");
+  CK(cudaSetDevice(ctx->device));
+  free_slots(ctx);
+  if (nslots == 0) return OSP_OK;
+  if (!ctx->qstream) {
+    CK(cudaStreamCreateWithFlags(&ctx->qstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_scores, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_queries, cudaEventDisableTiming));
+    // the scores as they stand are the first snapshot queries wait for
+    CK(cudaEventRecord(ctx->ev_scores, ctx->stream));
+  }
+  const int64_t nc = ctx->nc;
+  ctx->qslots.resize(nslots);
+  for (auto& q : ctx->qslots) {
+    TopkScratch& t = q.t;
+    osp_status s = OSP_OK;
+#define QL(p, cnt)                                               \
+  do {                                                           \
+    s = dalloc(ctx, &(p), (size_t)(cnt), 0, &ctx->qallocs);      \
+    if (s != OSP_OK) {                                           \
+      free_slots(ctx);                                           \
+      return s;                                                  \
+    }                                                            \
+  } while (0)
+    QL(q.col, nc);
+    QL(t.st, 1);
+    QL(t.hist, 4096);
+    QL(t.blk_a, nc / kTopkChunk + 2);
+    QL(t.blk_b, nc / kTopkChunk + 2);
+    QL(t.keys, kTopkMaxK + kTopkCand);
+    QL(t.ids, kTopkMaxK + kTopkCand);
+    QL(t.out_ids, kTopkMaxK);
+    QL(t.out_sc, kTopkMaxK);
+    QL(t.out_k, 1);
+    QL(t.dsum, 1);
+#undef QL
+    CK(cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return OSP_OK;
+}
+
+osp_status osp_topk_async(osp_ctx* ctx, int32_t slot, int32_t seed_idx, int32_t k, int normalize) {
+  osp_status s = check_ready(ctx, true);
+  if (s != OSP_OK) return s;
+  if (slot < 0 || slot >= (int)ctx->qslots.size()) return fail(ctx, OSP_EINVAL, "no such query slot");
+  QuerySlot& q = ctx->qslots[slot];
+  if (q.busy) return fail(ctx, OSP_ESTATE, "query slot busy (collect it with osp_topk_wait)");
+  if (seed_idx < 0 || seed_idx >= ctx->S || k <= 0 || k > kTopkMaxK)
+    return fail(ctx, OSP_EINVAL, "bad seed index or k outside [1, 4096]");
+  cudaStream_t qs = ctx->qstream;
+  CK(cudaStreamWaitEvent(qs, ctx->ev_scores, 0));
+  s = enqueue_gather(ctx, qs, seed_idx, q.col);
+  if (s == OSP_OK) s = enqueue_topk(ctx, qs, q.col, (int)ctx->n, k, normalize, q.t);
+  if (s != OSP_OK) return s;
+  CK(cudaEventRecord(q.done, qs));
+  CK(cudaEventRecord(ctx->ev_queries, qs));
+  q.busy = 1;
+  q.k = k;
+  return OSP_OK;
+}
+
+osp_status osp_topk_wait(osp_ctx* ctx, int32_t slot, int32_t* ids, double* scores, int32_t* k_out) {
+  if (!ctx) return OSP_EINVAL;
+  if (slot < 0 || slot >= (int)ctx->qslots.size()) return fail(ctx, OSP_EINVAL, "no such query slot");
+  QuerySlot& q = ctx->qslots[slot];
+  if (!q.busy) return fail(ctx, OSP_ESTATE, "query slot holds no query");
+  if (!ids || !scores || !k_out) return fail(ctx, OSP_EINVAL, "null output");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaEventSynchronize(q.done));
+  q.busy = 0;
+  int kk = 0;
+  CK(cudaMemcpy(&kk, q.t.out_k, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ids, q.t.out_ids, sizeof(int) * kk, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(scores, q.t.out_sc, sizeof(double) * kk, cudaMemcpyDeviceToHost));
+  *k_out = kk;
   return OSP_OK;
 }
 

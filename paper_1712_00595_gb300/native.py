@@ -30,7 +30,8 @@ EXPORTED = [
     "osp_query", "osp_query_device", "osp_topk", "osp_export_graph", "osp_get_size",
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
     "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
-    "osp_set_seed_iterations", "osp_get_schedule",
+    "osp_set_seed_iterations", "osp_get_schedule", "osp_query_slots", "osp_topk_async",
+    "osp_topk_wait",
 ]
 
 
@@ -100,6 +101,9 @@ def load_library(path: str = LIB_PATH):
             "osp_get_seed_stats": (C.c_int, [P, P, P, P, i32, P]),
             "osp_set_seed_iterations": (C.c_int, [P, P, i32]),
             "osp_get_schedule": (C.c_int, [P, P]),
+            "osp_query_slots": (C.c_int, [P, i32]),
+            "osp_topk_async": (C.c_int, [P, i32, i32, i32, C.c_int]),
+            "osp_topk_wait": (C.c_int, [P, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -257,6 +261,20 @@ class Engine:
             return self._check(self._L.osp_set_seed_iterations(self._h, None, 0))
         k = np.ascontiguousarray(k, np.int32)
         return self._check(self._L.osp_set_seed_iterations(self._h, _ptr(k), int(k.size)))
+
+    def query_slots(self, nslots):
+        return self._check(self._L.osp_query_slots(self._h, int(nslots)))
+
+    def topk_async(self, slot, k, seed_idx=0, normalize=False):
+        return self._check(self._L.osp_topk_async(self._h, int(slot), int(seed_idx), int(k),
+                                                  int(bool(normalize))))
+
+    def topk_wait(self, slot, k_max=4096):
+        ids = np.empty(k_max, np.int32)
+        sc = np.empty(k_max, np.float64)
+        got = C.c_int32(0)
+        self._check(self._L.osp_topk_wait(self._h, int(slot), _ptr(ids), _ptr(sc), C.byref(got)))
+        return ids[: got.value], sc[: got.value]
 
     def get_schedule(self):
         """(task items, long-list threshold, piece length, node items) in force."""

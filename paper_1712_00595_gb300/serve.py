@@ -1,0 +1,156 @@
+"""Serving loop: a stream of update and query requests over one engine.
+
+Requests carry arrival times. The server walks them in arrival order:
+
+* consecutive update requests that have arrived are merged into one engine
+  batch (up to the engine's batch limit), so one propagation serves all of
+  them;
+* a query (top-k for one or more tracked seeds) takes free query slots, one
+  per seed, and is enqueued on the engine's query stream. It reads the scores
+  after exactly the updates that arrived before it, because a query is never
+  merged past: the next batch is applied only after the query is enqueued,
+  and that batch's propagation waits for it on the device. Its ingest, merge
+  and offset kernels run while the query does.
+
+Results are therefore the same as serving the requests one at a time, up to
+the truncation of OSP-T (merging update requests changes where the series of
+Algorithm 1 is cut, within its error bound). The number of slots is the HBM
+budget for queries divided by the bytes of one slot.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import native as N
+
+
+@dataclass
+class Update:
+    t: float          # arrival time (s from the start of the run)
+    ops: np.ndarray   # UPDATE_DTYPE
+
+
+@dataclass
+class Query:
+    t: float
+    seeds: tuple      # seed indices (columns of the engine's seed block)
+    k: int = 100
+
+
+@dataclass
+class Result:
+    request: object
+    done: float = 0.0                             # completion time (s from the start)
+    batch: int = -1                               # updates: the engine batch that applied them
+    topk: list = field(default_factory=list)      # queries: (ids, scores) per seed
+
+    @property
+    def latency(self):
+        return self.done - self.request.t
+
+
+def slot_bytes(n_slots_nodes: int) -> int:
+    """Device bytes of one query slot for an engine of n node slots."""
+    return 8 * n_slots_nodes + 160 * 1024
+
+
+class Server:
+    def __init__(self, engine: N.Engine, slots: int, eps: float, max_ops: int = 0):
+        self.eng = engine
+        self.slots = int(slots)
+        self.eps = eps
+        self.max_ops = int(max_ops) or int(N.load_library().osp_max_batch())
+        engine.query_slots(self.slots)
+        self.batches = []      # sizes (ops) of the engine batches formed
+
+    def run(self, requests, realtime=True):
+        """Serve ``requests`` (sorted by arrival). realtime: a request is taken
+        only once the wall clock reaches its arrival time; otherwise all are
+        available at once (closed loop)."""
+        reqs = list(requests)
+        res = [Result(r) for r in reqs]
+        free = list(range(self.slots))
+        inflight = []          # (slot, result index, position in the query's seed list)
+        t0 = time.perf_counter()
+        clock = (lambda: time.perf_counter() - t0) if realtime else (lambda: float("inf"))
+
+        def collect_all():
+            for slot, ri, pos in inflight:
+                ids, sc = self.eng.topk_wait(slot)
+                res[ri].topk[pos] = (ids, sc)
+                res[ri].done = max(res[ri].done, time.perf_counter() - t0)
+                free.append(slot)
+            inflight.clear()
+
+        i = 0
+        while i < len(reqs):
+            if reqs[i].t > clock():
+                if inflight:
+                    collect_all()
+                    continue
+                time.sleep(max(0.0, reqs[i].t - clock()))
+                continue
+            r = reqs[i]
+            if isinstance(r, Query):
+                res[i].topk = [None] * len(r.seeds)
+                for pos, s in enumerate(r.seeds):
+                    if not free:
+                        collect_all()
+                    slot = free.pop()
+                    self.eng.topk_async(slot, r.k, seed_idx=int(s))
+                    inflight.append((slot, i, pos))
+                i += 1
+                continue
+            # merge the consecutive arrived updates that fit in one batch
+            j, ops = i, 0
+            while (j < len(reqs) and isinstance(reqs[j], Update) and reqs[j].t <= clock()
+                   and ops + reqs[j].ops.size <= self.max_ops):
+                ops += reqs[j].ops.size
+                j += 1
+            if j == i:  # a single request larger than the limit is an error of the caller
+                raise ValueError("update request of %d ops exceeds the batch limit %d"
+                                 % (reqs[i].ops.size, self.max_ops))
+            batch = np.concatenate([reqs[q].ops for q in range(i, j)])
+            self.eng.apply_updates(batch, self.eps)
+            now = time.perf_counter() - t0
+            for q in range(i, j):
+                res[q].done = now
+                res[q].batch = len(self.batches)
+            self.batches.append(int(batch.size))
+            collect_all()   # the queries enqueued before this batch have finished
+            i = j
+        collect_all()
+        return res
+
+
+def latency_summary(results, kind):
+    lat = np.array([r.latency for r in results if isinstance(r.request, kind)])
+    if lat.size == 0:
+        return None
+    return {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3)}
+
+
+def poisson_requests(rate, count, n_seeds, update_stream, query_frac, seed, k=100,
+                     max_query_seeds=32):
+    """``count`` requests with exponential inter-arrival times at ``rate`` per
+    second: a fraction ``query_frac`` are top-k queries for 1..max_query_seeds
+    distinct tracked seeds, the rest take the next batch of ``update_stream``."""
+    from .workloads import rng_for
+    rng = rng_for(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    out = []
+    it = iter(update_stream)
+    for a in t:
+        if rng.random() < query_frac:
+            m = int(rng.integers(1, max_query_seeds + 1))
+            out.append(Query(float(a), tuple(int(x) for x in rng.choice(n_seeds, m, replace=False)), k))
+        else:
+            nxt = next(it, None)
+            if nxt is None:
+                break
+            out.append(Update(float(a), nxt))
+    return out
