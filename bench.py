@@ -73,8 +73,11 @@ def parse():
                    help="CPU time bound of the cpu_baseline sample (whole batches)")
     p.add_argument("--launch", default="graphs", choices=["graphs", "eager"],
                    help="batch kernels replayed from CUDA graphs, or launched one by one")
-    p.add_argument("--workload", default="rmat20", choices=["rmat20"] + sorted(MULTI_WORKLOADS),
+    p.add_argument("--workload", default="rmat20",
+                   choices=["rmat20", "serve22"] + sorted(MULTI_WORKLOADS),
                    help="rmat20: the one-seed headline; the others track many seeds at once")
+    p.add_argument("--serve-policy", default="latest", choices=["ordered", "latest"],
+                   help="serve22: queries read in arrival order, or the newest scores")
     p.add_argument("--log2n", type=int, default=0,
                    help="several-seed workloads: nodes 2^log2n (edges scaled alike; 0 = full size)")
     p.add_argument("--fp64-seeds", type=int, default=8,
@@ -602,11 +605,74 @@ def run_multi(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+def run_serve(args, rank, world):
+    """The serving loop on R-MAT scale 22 with 256 tracked seeds: Poisson
+    arrivals at 2,000 requests/s, half update requests (log-uniform 1..5,000
+    ops, half insertions) and half top-100 queries for 1..32 seeds."""
+    import torch
+
+    from paper_1712_00595_gb300 import native as N
+    from paper_1712_00595_gb300 import serve as SV
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    log2n = args.log2n or 22
+    n_req, warm = 4000, 200
+    rate, qfrac, S = 2000.0, 0.5, 256
+    base = W.BASE_SEED + 7
+    gen, src, dst = W.rmat_graph(log2n, 16 << log2n, seed=base)
+    n = gen.n
+    seeds = W.rng_for(base + 1).choice(n, S, replace=False).astype(np.int32)
+    sizes = W.log_uniform_sizes(n_req + warm, 1, 5000, seed=base + 2)
+    stream = W.sized_update_stream(src, dst, n, sizes, base + 3, gen.sample)
+    reqs = SV.poisson_requests(rate, n_req + 2 * warm, S, stream, qfrac, base + 4)
+    eng = N.Engine(precision=N.OSP_PREC_FP32_ACC64, device=local, use_graphs=True)
+    eng.load_graph(n, src, dst)
+    eng.set_seeds(seeds, C_RESTART)
+    eng.init_scores(1e-8)
+    nc = n + n // 4 + 4096
+    budget = 2 << 30
+    slots = int(min(64, budget // SV.slot_bytes(nc)))
+    srv = SV.Server(eng, slots, eps=1e-6, policy=args.serve_policy)
+    srv.run(reqs[:warm], realtime=False)  # first graph captures, warm caches
+    t_first = reqs[warm].t
+    timed = [type(r)(r.t - t_first, *[getattr(r, f) for f in r.__dataclass_fields__ if f != "t"])
+             for r in reqs[warm:]]
+    b0 = len(srv.batches)
+    t0 = time.perf_counter()
+    got = srv.run(timed, realtime=True)
+    wall = time.perf_counter() - t0
+    eng.close()
+    upd = SV.latency_summary(got, SV.Update)
+    qry = SV.latency_summary(got, SV.Query)
+    sizes_b = srv.batches[b0:]
+    out = {
+        "metric": "served requests/s with p50/p99 latency (update batches and top-100 queries)",
+        "value": len(got) / wall, "unit": "requests/s", "n_gpus": world, "steps": len(got),
+        "warmup": warm, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "accumulate": "f64", "data": "synthetic",
+        "config": {"workload": "serve22" if log2n == 22 else "serve_at_log2n_%d" % log2n,
+                   "graph": "R-MAT scale %d, ids permuted" % log2n, "nodes": n, "edges": int(src.size),
+                   "tracked_seeds": S, "offered_rate": rate, "query_fraction": qfrac,
+                   "update_ops": "log-uniform 1..5000, half insertions", "query": "top-100 of 1..32 seeds",
+                   "eps": 1e-6, "query_slots": slots, "query_hbm_budget_bytes": budget,
+                   "policy": args.serve_policy},
+        "latency": {"update": upd, "query": qry},
+        "offered_seconds": timed[-1].t, "served_seconds": wall,
+        "engine_batches": len(sizes_b),
+        "ops_per_batch_mean": float(np.mean(sizes_b)) if sizes_b else 0.0,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "serve22":
+        run_serve(args, rank, world)
     elif args.workload != "rmat20":
         run_multi(args, rank, world)
     else:

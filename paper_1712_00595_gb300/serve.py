@@ -16,6 +16,12 @@ Results are therefore the same as serving the requests one at a time, up to
 the truncation of OSP-T (merging update requests changes where the series of
 Algorithm 1 is cut, within its error bound). The number of slots is the HBM
 budget for queries divided by the bytes of one slot.
+
+With policy "latest" the server instead merges every arrived update request
+(in batches up to the engine limit) before the queries that arrived with them,
+and answers those queries on the newest scores; each query records how many
+engine batches it saw, so its result equals the top-k after those batches
+applied one by one. This trades arrival-order reads for far fewer batches.
 """
 from __future__ import annotations
 
@@ -45,6 +51,7 @@ class Result:
     request: object
     done: float = 0.0                             # completion time (s from the start)
     batch: int = -1                               # updates: the engine batch that applied them
+    seen: int = -1                                # queries: engine batches applied before them
     topk: list = field(default_factory=list)      # queries: (ids, scores) per seed
 
     @property
@@ -58,13 +65,18 @@ def slot_bytes(n_slots_nodes: int) -> int:
 
 
 class Server:
-    def __init__(self, engine: N.Engine, slots: int, eps: float, max_ops: int = 0):
+    def __init__(self, engine: N.Engine, slots: int, eps: float, max_ops: int = 0,
+                 policy: str = "ordered"):
+        if policy not in ("ordered", "latest"):
+            raise ValueError("policy is 'ordered' or 'latest'")
+        self.policy = policy
         self.eng = engine
         self.slots = int(slots)
         self.eps = eps
         self.max_ops = int(max_ops) or int(N.load_library().osp_max_batch())
         engine.query_slots(self.slots)
         self.batches = []      # sizes (ops) of the engine batches formed
+        self.batch_requests = []  # request indices (of the last run) merged into each batch
 
     def run(self, requests, realtime=True):
         """Serve ``requests`` (sorted by arrival). realtime: a request is taken
@@ -85,6 +97,8 @@ class Server:
                 free.append(slot)
             inflight.clear()
 
+        if self.policy == "latest":
+            return self._run_latest(reqs, res, free, inflight, t0, clock, collect_all)
         i = 0
         while i < len(reqs):
             if reqs[i].t > clock():
@@ -95,6 +109,7 @@ class Server:
                 continue
             r = reqs[i]
             if isinstance(r, Query):
+                res[i].seen = len(self.batches)
                 res[i].topk = [None] * len(r.seeds)
                 for pos, s in enumerate(r.seeds):
                     if not free:
@@ -113,14 +128,60 @@ class Server:
             if j == i:  # a single request larger than the limit is an error of the caller
                 raise ValueError("update request of %d ops exceeds the batch limit %d"
                                  % (reqs[i].ops.size, self.max_ops))
-            batch = np.concatenate([reqs[q].ops for q in range(i, j)])
-            self.eng.apply_updates(batch, self.eps)
-            now = time.perf_counter() - t0
-            for q in range(i, j):
-                res[q].done = now
-                res[q].batch = len(self.batches)
-            self.batches.append(int(batch.size))
+            self._apply(reqs, res, list(range(i, j)), t0)
             collect_all()   # the queries enqueued before this batch have finished
+            i = j
+        collect_all()
+        return res
+
+    def _apply(self, reqs, res, idx, t0):
+        batch = np.concatenate([reqs[q].ops for q in idx])
+        self.eng.apply_updates(batch, self.eps)
+        now = time.perf_counter() - t0
+        for q in idx:
+            res[q].done = now
+            res[q].batch = len(self.batches)
+        self.batches.append(int(batch.size))
+        self.batch_requests.append(list(idx))
+
+    def _run_latest(self, reqs, res, free, inflight, t0, clock, collect_all):
+        i = 0
+        while i < len(reqs):
+            if reqs[i].t > clock():
+                if inflight:
+                    collect_all()
+                    continue
+                time.sleep(max(0.0, reqs[i].t - clock()))
+                continue
+            j = i
+            while j < len(reqs) and reqs[j].t <= clock():
+                j += 1
+            ups = [q for q in range(i, j) if isinstance(reqs[q], Update)]
+            qs = [q for q in range(i, j) if isinstance(reqs[q], Query)]
+            cur, ops = [], 0
+            for q in ups:  # every arrived update, in batches up to the engine limit
+                if reqs[q].ops.size > self.max_ops:
+                    raise ValueError("update request of %d ops exceeds the batch limit %d"
+                                     % (reqs[q].ops.size, self.max_ops))
+                if ops + reqs[q].ops.size > self.max_ops:
+                    self._apply(reqs, res, cur, t0)
+                    collect_all()
+                    cur, ops = [], 0
+                cur.append(q)
+                ops += reqs[q].ops.size
+            if cur:
+                self._apply(reqs, res, cur, t0)
+                collect_all()
+            for q in qs:  # on the newest scores; they overlap the next batch
+                r = reqs[q]
+                res[q].seen = len(self.batches)
+                res[q].topk = [None] * len(r.seeds)
+                for pos, s in enumerate(r.seeds):
+                    if not free:
+                        collect_all()
+                    slot = free.pop()
+                    self.eng.topk_async(slot, r.k, seed_idx=int(s))
+                    inflight.append((slot, q, pos))
             i = j
         collect_all()
         return res

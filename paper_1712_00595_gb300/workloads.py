@@ -412,3 +412,40 @@ def node_op_stream(src, dst, n: int, batches: int, n_new: int, new_degree: int, 
         dead[victims] = True
         out.append(np.concatenate(parts))
     return out
+
+
+def sized_update_stream(src, dst, n: int, sizes, seed: int, sampler):
+    """One batch per entry of ``sizes``: half insertions of absent edges drawn
+    from ``sampler``, half deletions of edges of the initial graph (uniform),
+    valid in sequence. Absence and presence are checked against the initial
+    edge set and the keys inserted or deleted so far, so no batch rewrites the
+    whole edge set (inserted edges are never deleted again)."""
+    rng = rng_for(seed)
+    es = EdgeSet(src, dst)
+    inserted, deleted = set(), set()
+    out = []
+    for k in sizes:
+        k = int(k)
+        n_ins, n_del = k // 2, k - k // 2
+        ins = []
+        while len(ins) < n_ins:
+            u, v = sampler(2 * (n_ins - len(ins)) + 8)
+            ok = u != v
+            cand = edge_keys(u[ok], v[ok])
+            cand = cand[~es.contains(cand)]
+            for c in cand.tolist():
+                if c not in inserted:
+                    inserted.add(c)
+                    ins.append(c)
+                    if len(ins) == n_ins:
+                        break
+        dels = []
+        while len(dels) < n_del:
+            for c in es.keys[rng.integers(0, es.keys.size, 2 * (n_del - len(dels)) + 8)].tolist():
+                if c not in deleted:
+                    deleted.add(c)
+                    dels.append(c)
+                    if len(dels) == n_del:
+                        break
+        out.append(_pack(np.array(ins, np.uint64), np.array(dels, np.uint64), rng))
+    return out

@@ -88,6 +88,34 @@ def test_served_results_equal_requests_served_alone(realtime):
     assert all(g.done >= g.request.t for g in got)
 
 
+def test_latest_policy_matches_its_batches_applied_alone():
+    rng = np.random.default_rng(32)
+    n = 3000
+    src, dst = _graph(rng, n)
+    seeds = [0, 1, 7, 100, 2000]
+    reqs = _requests(rng, n, src, dst, seeds, 60)
+    eng = _engine(n, src, dst, seeds)
+    srv = SV.Server(eng, slots=3, eps=1e-12, policy="latest")
+    got = srv.run(reqs, realtime=False)
+    eng.close()
+    n_upd = sum(isinstance(r, SV.Update) for r in reqs)
+    assert len(srv.batches) < n_upd
+    # replay: the server's merged batches one by one; each query after the
+    # number of batches it saw
+    ref = _engine(n, src, dst, seeds)
+    applied = 0
+    order = sorted((g.seen, k) for k, g in enumerate(got) if isinstance(g.request, SV.Query))
+    for seen, k in order:
+        while applied < seen:
+            ref.apply_updates(np.concatenate([reqs[q].ops for q in srv.batch_requests[applied]]),
+                              1e-12)
+            applied += 1
+        r = reqs[k]
+        for pos, s in enumerate(r.seeds):
+            _same_topk(got[k].topk[pos], ref.topk(r.k, seed_idx=s))
+    ref.close()
+
+
 def test_query_slots_api():
     rng = np.random.default_rng(2)
     n = 500
