@@ -200,3 +200,42 @@ def test_multi_rejects_bad_seed_sets_and_seed_deletion():
         e16.set_seeds(np.array([3], np.int32), C_RESTART)
     assert e.value.status == N.OSP_ENOTSUP
     e16.close()
+
+
+import os  # noqa: E402
+
+FULL = pytest.mark.skipif(os.environ.get("OSP_FULLSIZE") != "1",
+                          reason="full-size workloads run with OSP_FULLSIZE=1 (minutes of generation)")
+
+
+@pytest.mark.parametrize("workload,log2n", [
+    ("chunglu22_s64", 18), ("rmat24_s256", 17),
+    pytest.param("chunglu22_s64", 22, marks=FULL), pytest.param("rmat24_s256", 24, marks=FULL)])
+def test_seed_block_workloads_residual_certificate(workload, log2n):
+    """The seed-block workloads of the benchmark (generators and precisions as
+    bench.py runs them, at reduced size) through every batch. For sampled seeds
+    the FP64 residual rho = c e_s - (I - (1-c) B~^T) r of the final scores, which
+    bounds ||r - r*||_1 <= ||rho||_1 / c, must stay within what the stopping rule
+    and the rounding allow: the initial CPI leaves at most (1-c) eps_init (plus
+    float rounding of its unit mass), each batch at most (1-c) eps of untaken
+    tail, and the stored gather values and float in-list sums (pieces of at
+    most 256 terms) add at most u (1-c) ||q_offset||_1 / c per batch, with
+    u = 2^-8 + 2^-16 for bf16 and 2^-16 for float."""
+    import bench
+
+    cfg, n, src, dst, seeds, stream, _ = bench.make_multi_workload(workload, log2n)
+    prec = {"fp32": N.OSP_PREC_FP32_ACC64, "bf16": N.OSP_PREC_BF16_ACC64}[cfg["precision"]]
+    unit = (2.0 ** -8 if cfg["precision"] == "bf16" else 0.0) + 2.0 ** -16
+    eps, eps_init = cfg["eps"], 1e-8
+    eng = make_engine(prec, n, src, dst, seeds, eps_init, use_graphs=True)
+    sample = np.linspace(0, len(seeds) - 1, 4).astype(int)
+    bound = np.full(len(seeds), (1 - C_RESTART) * eps_init + 2.0 ** -16 * (1 - C_RESTART) + 1e-9)
+    for ops in stream:
+        eng.apply_updates(ops, eps)
+        _, q, _ = eng.get_seed_stats()
+        bound += (1 - C_RESTART) * eps + unit * (1 - C_RESTART) / C_RESTART * q
+    ptr, idx = eng.export_graph(0)
+    for j in sample:
+        rho = O.residual_l1(ptr, idx, int(seeds[j]), C_RESTART, eng.query(int(j)))
+        assert rho <= bound[j], (j, rho, bound[j])
+    eng.close()
