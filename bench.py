@@ -47,7 +47,7 @@ STREAM_SEED_OFFSET = 202
 MULTI_WORKLOADS = {
     # undirected Chung-Lu (exponent 2.1, mean degree 16): 4,194,304 nodes,
     # 33,554,432 undirected edges stored in both directions; 64 uniform seeds;
-    # batches of log-uniform 10 .. 8,192 undirected edges (each = 2 directed ops,
+    # batches of log-uniform 10 .. 10,000 undirected edges (each = 2 directed ops,
     # half insertions, half deletions); FP32 gather vectors, FP64 sums
     "chunglu22_s64": {"graph": "chunglu", "log2n": 22, "m": 33554432, "S": 64,
                       "precision": "fp32", "eps": 1e-6, "batches": 50},
@@ -478,11 +478,11 @@ def make_multi_workload(name, log2n):
         gen, lo, hi = W.chung_lu_graph(n, m, seed=base)
         src = np.concatenate([lo, hi])
         dst = np.concatenate([hi, lo])
-        sizes = W.log_uniform_sizes(batches, 10, 8192, seed=base + 300)
+        sizes = W.log_uniform_sizes(batches, 10, 10000, seed=base + 300)
         stream = W.undirected_update_stream(lo, hi, n, sizes, base + 301, gen.sample)
         seeds = W.rng_for(base + 302).choice(n, S, replace=False).astype(np.int32)
         desc = ("undirected Chung-Lu (exponent 2.1, mean degree 16), both directions stored; "
-                "batches of log-uniform 10..8192 undirected edges, half insertions")
+                "batches of log-uniform 10..10000 undirected edges, half insertions")
     else:
         gen, src, dst = W.rmat_graph(log2n, m, seed=base)
         seeds = W.rng_for(base + 302).choice(n, S, replace=False).astype(np.int32)

@@ -163,14 +163,15 @@ osp_status osp_set_seeds(osp_ctx *ctx, const int32_t *seeds, int32_t S, double c
  * maxima over the seeds (osp_get_seed_stats gives each seed's). */
 osp_status osp_init_scores(osp_ctx *ctx, double eps, osp_batch_stats *stats);
 
-/* Apply one batch of U updates (host array, U <= osp_max_batch()) and update
+/* Apply one batch of U updates (host array, U <= 2^22, see osp_max_batch) and update
  * the scores by OSP / OSP-T (Algorithm 1):
  *   q_offset = (1-c)(B~^T - A~^T) r_old,  r_new = r_old + sum_i ((1-c)B~^T)^i q_offset,
  * stopping after the first term with ||x(i)||_1 <= eps. Exact OSP is a small
  * eps (Sec. 3.1 suggests 1e-9); OSP-T is a larger one (Sec. 3.2). The graph
  * update is applied in full even when the scores return ENOCONV. stats may be
- * NULL. Returns EINVAL (state unchanged, stats->bad_op set) for an invalid
- * batch. Synchronises the context stream before returning. */
+ * NULL. Returns EINVAL (stats->bad_op set) for an invalid batch, with the
+ * state unchanged when U <= osp_max_batch() (larger batches: see there).
+ * Synchronises the context stream before returning. */
 osp_status osp_apply_updates(osp_ctx *ctx, const osp_update *ops, int64_t U, double eps,
                              osp_batch_stats *stats);
 
@@ -178,7 +179,13 @@ osp_status osp_apply_updates(osp_ctx *ctx, const osp_update *ops, int64_t U, dou
 osp_status osp_apply_updates_device(osp_ctx *ctx, const osp_update *ops_device, int64_t U,
                                     double eps, osp_batch_stats *stats);
 
-/* Largest U accepted by one apply call. */
+/* Largest U applied as one unit (16,384): an invalid op leaves the state
+ * unchanged. Apply calls accept up to 2^22 ops; a larger batch is ingested
+ * and merged in consecutive sub-batches of osp_max_batch() ops, all against
+ * the same r_old (their offsets add up to the whole batch's offset), followed
+ * by one propagation. If an op of a later sub-batch is invalid, the
+ * sub-batches before it stay applied and propagated, the call returns
+ * OSP_EINVAL and stats->bad_op gives the op's index. */
 int64_t osp_max_batch(void);
 
 /* Copy the scores of seed seed_idx to out[0 .. n) (host). normalize != 0 returns

@@ -16,7 +16,8 @@
 
 namespace osp {
 
-constexpr int kMaxBatch = 16384;        // ops per apply call (keys pack the op index in 14 bits)
+constexpr int kMaxBatch = 16384;        // ops per sub-batch (keys pack the op index in 14 bits)
+constexpr long long kMaxLargeBatch = 1ll << 22;  // ops per apply call, in sub-batches of kMaxBatch
 constexpr int kMaxNodes = (1 << 25) - 1; // ids fit in 25 bits
 constexpr int kNoPos = 0x7F7F7F7F;       // del_pos of a node not deleted by the batch (memset 0x7F)
 constexpr int kLight = 32;               // lists up to this length are walked by one lane

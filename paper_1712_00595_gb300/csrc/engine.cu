@@ -500,9 +500,10 @@ osp_status check_ready(osp_ctx* ctx, bool need_scores) {
 
 // Ingest, merge and offset of one batch (U < 0: k_ingest reads the size from
 // the control block, as a graph replay does).
-osp_status enqueue_update(osp_ctx* ctx, const osp_update* ops_dev, int U, int Np) {
+osp_status enqueue_update(osp_ctx* ctx, const osp_update* ops_dev, int U, int Np,
+                          bool cont = false) {
   const int g = ctx->num_sms * 4;
-  k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d, cont ? 1 : 0);
   ++ctx->launches;
   k_ingest<<<1, 1024, (size_t)Np * 8, ctx->stream>>>(ctx->d, ops_dev, U);
   ++ctx->launches;
@@ -558,6 +559,69 @@ osp_status capture_graphs(osp_ctx* ctx, int Np, double eps, osp_ctx::GraphPair* 
   out->launches = ctx->launches;
   ctx->launches = before;
   return OSP_OK;
+}
+
+// A batch of more than kMaxBatch ops: consecutive sub-batches of kMaxBatch ops
+// are ingested and merged one after the other, all against the same r_old, so
+// their offsets add up to the offset of the whole batch; one propagation
+// follows. ops is a device pointer, or a host one when host != 0 (staged per
+// sub-batch through pinned memory). An invalid op stops the sequence: the
+// sub-batches before it stay applied and are propagated.
+osp_status apply_large(osp_ctx* ctx, const osp_update* ops, bool host, int64_t U, double eps,
+                       osp_batch_stats* st) {
+  if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
+  ctx->launches = 0;
+  const int64_t m_before = ctx->m;
+  int64_t bad = -1;
+  osp_status err = OSP_OK;
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  for (int64_t s0 = 0; s0 < U; s0 += kMaxBatch) {
+    const int u = (int)std::min<int64_t>(kMaxBatch, U - s0);
+    osp_status s = reserve_for_batch(ctx, u);
+    if (s != OSP_OK) {
+      err = s;
+      break;
+    }
+    const osp_update* p = ops + s0;
+    if (host) {
+      std::memcpy(ctx->pinned, p, sizeof(osp_update) * (size_t)u);
+      CK(cudaMemcpyAsync(ctx->ops_stage, ctx->pinned, sizeof(osp_update) * (size_t)u,
+                         cudaMemcpyHostToDevice, ctx->stream));
+      p = ctx->ops_stage;
+    }
+    int Np = 2;
+    while (Np < u) Np <<= 1;
+    s = enqueue_update(ctx, p, u, Np, s0 > 0);
+    if (s != OSP_OK) return s;
+    Ctl h;
+    s = read_ctl(ctx, &h);  // also orders the pinned buffer's reuse
+    if (s != OSP_OK) return s;
+    if (h.status == OSP_EINVAL) {
+      bad = s0 + h.bad_op;
+      h.status = 0;
+      s = write_ctl(ctx, h);
+      if (s != OSP_OK) return s;
+      break;
+    }
+    if (h.status != 0) {
+      ctx->broken = true;
+      return fail(ctx, (osp_status)h.status, "device error in a sub-batch");
+    }
+    ctx->n = h.n;
+    ctx->m = h.m + h.m_delta;  // live entries so far (the change is folded in at the end)
+    ctx->top_r = h.pool_top_r;
+    ctx->top_c = h.pool_top_c;
+  }
+  osp_status s = run_propagation(ctx, eps, ctx->nc - 1, ctx->m);
+  if (s != OSP_OK) return s;
+  s = finish_call(ctx, m_before, st);
+  if (bad >= 0) {
+    if (st) st->bad_op = bad;
+    return fail(ctx, OSP_EINVAL, "invalid op " + std::to_string(bad) +
+                                     "; the sub-batches before it were applied");
+  }
+  if (err != OSP_OK) return fail(ctx, err, ctx->err + " (the sub-batches before it were applied)");
+  return s;
 }
 
 osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, double eps,
@@ -1035,7 +1099,7 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
 
 // x(0) = c e_s per seed, with the scores cleared.
 osp_status enqueue_cpi_start(osp_ctx* ctx) {
-  k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d);
+  k_reset_batch<<<1, 1, 0, ctx->stream>>>(ctx->d, 0);
   ++ctx->launches;
   if (ctx->S > 1) {
     const Multi& M = ctx->d.mu;
@@ -1126,8 +1190,9 @@ osp_status osp_apply_updates_device(osp_ctx* ctx, const osp_update* ops_device, 
                                     double eps, osp_batch_stats* stats) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
-  if (U < 0 || U > kMaxBatch) return fail(ctx, OSP_EINVAL, "batch size outside [0, osp_max_batch()]");
+  if (U < 0 || U > kMaxLargeBatch) return fail(ctx, OSP_EINVAL, "batch size outside [0, 2^22]");
   if (U > 0 && !ops_device) return fail(ctx, OSP_EINVAL, "null ops");
+  if (U > kMaxBatch) return apply_large(ctx, ops_device, false, U, eps, stats);
   return apply_common(ctx, ops_device, U, eps, stats);
 }
 
@@ -1135,8 +1200,9 @@ osp_status osp_apply_updates(osp_ctx* ctx, const osp_update* ops, int64_t U, dou
                              osp_batch_stats* stats) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
-  if (U < 0 || U > kMaxBatch) return fail(ctx, OSP_EINVAL, "batch size outside [0, osp_max_batch()]");
+  if (U < 0 || U > kMaxLargeBatch) return fail(ctx, OSP_EINVAL, "batch size outside [0, 2^22]");
   if (U > 0 && !ops) return fail(ctx, OSP_EINVAL, "null ops");
+  if (U > kMaxBatch) return apply_large(ctx, ops, true, U, eps, stats);
   if (U > 0) {
     const size_t bytes = sizeof(osp_update) * (size_t)U;
     std::memcpy(ctx->pinned, ops, bytes);

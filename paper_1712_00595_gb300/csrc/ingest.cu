@@ -152,11 +152,18 @@ __device__ void emit_groups(const unsigned long long* skey, int N, int per, int 
 
 }  // namespace
 
-__global__ void k_reset_batch(Dev d) {
+// cont != 0: a later sub-batch of one large batch. The offset accumulated so
+// far (xacc, stamps, first frontier), the edge-count change and the edit
+// counts carry over; only the per-sub-batch records restart.
+__global__ void k_reset_batch(Dev d, int cont) {
   Ctl* c = d.ctl;
   c->status = 0;
   c->bad_op = -1;
   c->n_old = c->n;
+  c->n_rec_r = 0;
+  c->n_rec_c = 0;
+  c->n_del = 0;
+  if (cont) return;
   c->m_delta = 0;
   c->net_ins = 0;
   c->net_del = 0;

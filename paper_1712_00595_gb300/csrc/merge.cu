@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(1024) k_merge_pieces(Dev d, double beta) {
     for (int i = 0; i < 32; ++i) t += s_b[i];
     // the offset reaches at most `t` nodes; above n/beta the first step is
     // dense anyway and x(0) is collected by a scan instead of a queue
-    ctl->dense0 = (double)t > (double)ctl->n / beta;
+    ctl->dense0 |= (double)t > (double)ctl->n / beta;  // sticky over sub-batches
   }
 }
 
@@ -316,6 +316,9 @@ __global__ void k_merge_finish(Dev d) {
   ctl->m += ctl->m_delta;
   ctl->m_delta = 0;
   ctl->n_hubs = 0;
+  // a dense first frontier is rebuilt by the x(0) scan: drop entries queued by
+  // earlier sub-batches of the same batch
+  if (ctl->dense0) ctl->q_size[0] = 0;
 }
 
 // Pull-step plan, part 1: warp task t starts at the first node v with

@@ -73,7 +73,7 @@ class Server:
         self.eng = engine
         self.slots = int(slots)
         self.eps = eps
-        self.max_ops = int(max_ops) or int(N.load_library().osp_max_batch())
+        self.max_ops = int(max_ops) or N.MAX_APPLY_OPS
         engine.query_slots(self.slots)
         self.batches = []      # sizes (ops) of the engine batches formed
         self.batch_requests = []  # request indices (of the last run) merged into each batch

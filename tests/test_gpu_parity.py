@@ -258,6 +258,42 @@ def test_autotuned_schedule_gives_the_same_scores(seeds):
         assert l1(a, b) <= 1e-12
 
 
+def test_large_batch_in_sub_batches():
+    """A batch above osp_max_batch() is merged in sub-batches against the same
+    r_old with one propagation: exact OSP of the whole batch. An invalid op in a
+    later sub-batch leaves the earlier sub-batches applied and propagated."""
+    rng = np.random.default_rng(71)
+    n = 3000
+    src, dst = hub_graph(rng, n=n, m=60000, hub_in=2500, hub_out=900, mids=12)
+    gen = np.random.default_rng(5)
+    sampler = lambda k: (gen.integers(0, n, k), gen.integers(0, n, k))  # noqa: E731
+    big = W.sized_update_stream(src, dst, n, [40000, 40000], 3, sampler)
+    eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, eps_init=1e-13)
+    assert eng._L.osp_max_batch() == 16384
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o, _, _ = O.cpi(*cur, 0, C_RESTART, 1e-13)
+    st = eng.apply_updates(big[0], 1e-13)
+    assert g.apply(big[0], protect=(0,)) == -1
+    new = g.csr()
+    r_o, q, _, _ = O.osp(cur, new, r_o, C_RESTART, 1e-13)
+    assert st["qoff_l1"] == pytest.approx(np.abs(q).sum(), rel=1e-9, abs=1e-15)
+    check_graph(eng, g)
+    assert l1(eng.query(), r_o) <= 1e-10
+    cur = new
+    bad = big[1].copy()
+    bad[35000] = (0, n + 100, 0)  # insert to a node that does not exist
+    st = eng.apply_updates(bad, 1e-13, allow=(N.OSP_EINVAL,))
+    assert eng.last_status == N.OSP_EINVAL and st["bad_op"] == 35000
+    done = 2 * 16384  # the two sub-batches before the one holding op 35000
+    assert g.apply(bad[:done], protect=(0,)) == -1
+    new = g.csr()
+    r_o, _, _, _ = O.osp(cur, new, r_o, C_RESTART, 1e-13)
+    check_graph(eng, g)
+    assert l1(eng.query(), r_o) <= 1e-10
+    eng.close()
+
+
 def test_invalid_batches_rejected_state_unchanged():
     rng = np.random.default_rng(9)
     n = 50
@@ -411,8 +447,8 @@ def test_max_size_batch():
     r0, _, _ = O.cpi(*old, 0, C_RESTART, 1e-10)
     r1, _, _, _ = O.osp(old, g.csr(), r0, C_RESTART, 1e-6, force_iters=st["iterations"])
     assert l1(eng.query(), r1) <= 1e-5
-    with pytest.raises(N.OspError):
-        eng.apply_updates(np.zeros(U + 1, W.UPDATE_DTYPE), 1e-6)
+    with pytest.raises(N.OspError):  # above what one call accepts (sub-batches included)
+        eng.apply_updates(np.zeros(N.MAX_APPLY_OPS + 1, W.UPDATE_DTYPE), 1e-6)
     eng.close()
 
 
