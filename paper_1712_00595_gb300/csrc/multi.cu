@@ -7,7 +7,8 @@
 //            (Sec. 3.1, 3.3): row u adds (1-c) R_old[u] / d'_u to every entry
 //            of its new out-list and subtracts (1-c) R_old[u] / d_u from every
 //            entry of its old out-list (old lists stay readable: the merge
-//            writes new lists out of place). Targets get this call's stamp.
+//            writes new lists out of place); an entry in both lists gets the
+//            difference in one addition. Targets get this call's stamp.
 //   x(0)     one pass over all nodes: stamped rows move from xacc into R and
 //            the first gather block y(0) = x(0) (1-c) / d; other rows of y(0)
 //            are written as zero.
@@ -282,7 +283,8 @@ __global__ void __launch_bounds__(1024) k_offset_multi_plan(Dev d) {
 }
 
 // Warp per offset item: R_old[u] times -(1-c)/d_u into xacc over the old
-// out-list entries, times +(1-c)/d'_u over the new ones; stamps the targets.
+// out-list entries, times +(1-c)/d'_u over the new ones (one combined term
+// for an entry in both lists); stamps the targets.
 template <int K>
 __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
   constexpr int Sp = 32 * K;
@@ -315,19 +317,22 @@ __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
       int a = 0;
       double wgt = 0.0;
       if (e < e1) {
+        // an entry kept in the new list carries both terms at once:
+        // (1-c)(1/d' - 1/d), zero when the degree did not change
         if (e < L) {
           a = oldl[e];
-          wgt = -wa;
+          wgt = contains_i(newl, dp, a) ? wb - wa : -wa;
         } else {
           a = newl[e - L];
-          wgt = wb;
+          wgt = contains_i(oldl, L, a) ? 0.0 : wb;
         }
       }
       if (!OSP_GUARD(ctl, a >= 0 && a < d.nc, "multi offset target", c, e, a)) a = 0;
       const int cnt = min(32, e1 - eb);
       for (int j = 0; j < cnt; ++j) {
-        const int aj = __shfl_sync(0xffffffffu, a, j);
         const double wj = __shfl_sync(0xffffffffu, wgt, j);
+        if (wj == 0.0) continue;  // warp-uniform
+        const int aj = __shfl_sync(0xffffffffu, a, j);
         double* row = d.mu.xacc + (size_t)aj * Sp + lane * K;
 #pragma unroll
         for (int k = 0; k < K; ++k)
