@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU time bound of the cpu_baseline sample (whole batches)")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep the default pull-step schedule (osp_init_scores tunes it otherwise)")
     p.add_argument("--launch", default="graphs", choices=["graphs", "eager"],
                    help="batch kernels replayed from CUDA graphs, or launched one by one")
     p.add_argument("--workload", default="rmat20",
@@ -336,7 +338,8 @@ def run_ours(args, rank, world):
     tstream = torch.cuda.Stream(device=dev)
 
     def new_engine(prec, graphs=args.launch == "graphs"):
-        e = N.Engine(precision=prec, device=local, stream=tstream.cuda_stream, use_graphs=graphs)
+        e = N.Engine(precision=prec, device=local, stream=tstream.cuda_stream, use_graphs=graphs,
+                     autotune=args.autotune)
         e.load_graph(n, src, dst)
         e.set_seeds([seed], C_RESTART)
         e.init_scores(args.eps_init)
@@ -385,6 +388,7 @@ def run_ours(args, rank, world):
     st_us = eng.get_step_times()
     step_profile = {"x0": float(st_us[0]), "steps": [round(float(x), 1) for x in st_us[1:]]}
     r_mixed = eng.query()
+    schedule = eng.get_schedule()
     t_local = sum(ms) / 1e3
     t_max = dist_max(t_local, world)
     value = world * K / t_max
@@ -400,7 +404,7 @@ def run_ours(args, rank, world):
         "warmup": Wm, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "accumulate": "f64", "data": "synthetic",
         "config": dict(workload_config(args, n, len(src), seed, "fp32 products, fp64 accumulation"),
-                       launch=args.launch),
+                       launch=args.launch, schedule=list(schedule)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(),
                      "kernel": "k_propagate<float>", "peak_kind": peak_kind + " (hbm_gbs copy)",
