@@ -288,6 +288,30 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def rank_accuracy(r, ref, k=100):
+    """Spearman rank correlation of two score vectors (average ranks for ties)
+    and the overlap of their top-k sets (ids ranked by score, then id)."""
+    def ranks(x):
+        order = np.lexsort((np.arange(x.size), -x))
+        rk = np.empty(x.size, np.float64)
+        rk[order] = np.arange(x.size, dtype=np.float64)
+        # average the ranks of equal scores
+        xs = x[order]
+        bounds = np.flatnonzero(np.diff(xs)) + 1
+        starts = np.concatenate([[0], bounds])
+        ends = np.concatenate([bounds, [x.size]])
+        avg = (starts + ends - 1) / 2.0
+        rk[order] = np.repeat(avg, ends - starts)
+        return rk
+    a, b = ranks(np.asarray(r)), ranks(np.asarray(ref))
+    a -= a.mean()
+    b -= b.mean()
+    rho = float((a * b).sum() / np.sqrt((a * a).sum() * (b * b).sum()))
+    ta = set(np.lexsort((np.arange(r.size), -np.asarray(r)))[:k].tolist())
+    tb = set(np.lexsort((np.arange(ref.size), -np.asarray(ref)))[:k].tolist())
+    return {"spearman": rho, "top%d_overlap" % k: len(ta & tb) / k}
+
+
 def workload_config(args, n, m, seed, precision):
     return {"workload": "rmat%d_osp_t" % args.scale, "graph": "R-MAT scale %d (a,b,c,d=.57,.19,.19,.05), "
             "ids permuted" % args.scale, "nodes": n, "edges": m, "seed_node": int(seed),
@@ -429,16 +453,25 @@ def run_ours(args, rank, world):
                             "ms_propagation_per_step": sum(s["ms_propagate"] for s in st64) / K}
         out["l1_vs_fp64"] = float(np.abs(r_mixed - r64).sum())
         out["speedup_vs_fp64"] = value / world / out["fp64_path"]["value"]
+        # ---- near-exact scores after the same batches (FP64, eps 1e-12) ----
+        ex = new_engine(N.OSP_PREC_FP64)
+        run(ex, 1e-12, Wm)
+        r_exact = ex.query()
+        ex.close()
         # ---- OSP-T eps sweep (FP32 products / FP64 accumulation) ----
         sweep = []
         for eps in (1e-4, 1e-6, 1e-8):
             e = new_engine(N.OSP_PREC_FP32_ACC64)
             ms_e, st_e = run(e, eps, Wm)
+            r_e = e.query()
             e.close()
             sweep.append({"eps": eps, "batches_per_s": K / (sum(ms_e) / 1e3),
                           "iterations": float(np.mean([s["iterations"] for s in st_e])),
-                          "ms_propagation": sum(s["ms_propagate"] for s in st_e) / K})
+                          "ms_propagation": sum(s["ms_propagate"] for s in st_e) / K,
+                          "l1_vs_exact": float(np.abs(r_e - r_exact).sum()),
+                          "rank_vs_exact": rank_accuracy(r_e, r_exact)})
         out["eps_sweep"] = sweep
+        out["rank_accuracy_fp32_vs_fp64"] = rank_accuracy(r_mixed, r64)
         # ---- the other launch mode (graph replays vs one launch per kernel) ----
         e = new_engine(N.OSP_PREC_FP32_ACC64, graphs=args.launch != "graphs")
         ms_o, _ = run(e, args.eps, Wm)

@@ -59,3 +59,17 @@ def test_replica_max_over_ranks_gloo():
         assert p.exitcode == 0
     got = sorted(q.get() for _ in range(2))
     assert got == [(0, 2, 2.0), (1, 2, 2.0)]
+
+
+def test_rank_accuracy_matches_scipy_spearman():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    import numpy as np
+    rng = np.random.default_rng(0)
+    a = rng.random(2000)
+    b = a + rng.normal(0, 0.01, a.size)
+    b[:80] = b[0]  # ties
+    got = bench.rank_accuracy(a, b)
+    assert got["spearman"] == pytest.approx(scipy_stats.spearmanr(a, b).correlation, abs=1e-12)
+    top_a = set(np.argsort(-a, kind="stable")[:100].tolist())
+    assert bench.rank_accuracy(a, a) == {"spearman": 1.0, "top100_overlap": 1.0}
+    assert 0.0 <= got["top100_overlap"] <= 1.0 and len(top_a) == 100
