@@ -146,6 +146,9 @@ void osp_destroy(osp_ctx *ctx);
 osp_status osp_load_graph(osp_ctx *ctx, int64_t n, int64_t m, const int32_t *src,
                           const int32_t *dst, int undirected);
 
+/* Seed value selecting PageRank mode (osp_set_seeds with S = 1). */
+#define OSP_PAGERANK (-1)
+
 /* Set the seed node(s) and the restart probability c in (0, 1) (Eq. 1). Each of
  * the S seeds (1 <= S <= 256, distinct live ids, host array) gets its own RWR
  * vector r_j with q = e_{s_j}; seed_idx j of the query calls selects it.
@@ -154,7 +157,11 @@ osp_status osp_load_graph(osp_ctx *ctx, int64_t n, int64_t m, const int32_t *src
  * dense-block product; each column stops on its own test (Algorithm 1's loop
  * test per seed). Device memory for S > 1: about Sp (16 + 2 b_y) bytes per node
  * slot (b_y = 8 for FP64, 4 otherwise). A seed cannot be
- * deleted by a batch. Invalidates scores. */
+ * deleted by a batch. Invalidates scores.
+ * PageRank mode (the paper's commented seed = -1 variant of Algorithm 1):
+ * S = 1 and seeds[0] = OSP_PAGERANK make q the uniform vector 1/n0 over the
+ * n0 nodes present now; q then stays fixed (OSP assumes a fixed q), so nodes
+ * added later have no restart mass and a deleted node keeps its c/n0. */
 osp_status osp_set_seeds(osp_ctx *ctx, const int32_t *seeds, int32_t S, double c);
 
 /* Compute scores from scratch by CPI (Sec. 2.2): x(0) = c e_s, stop after the

@@ -241,6 +241,12 @@ def dense_matrix(n, src, dst):
     return A
 
 
+def dense_rwr_q(n, src, dst, q, c):
+    """Eq. 1 with a general restart vector q: r = c (I - (1-c) A~^T)^-1 q (dense LU)."""
+    A = dense_matrix(n, src, dst)
+    return np.linalg.solve(np.eye(n) - (1.0 - c) * A.T, c * np.asarray(q, np.float64))
+
+
 def dense_rwr(n, src, dst, seed, c):
     """Eq. 1 solved directly: r = c (I - (1-c) A~^T)^-1 e_s, by LU with partial pivoting."""
     A = dense_matrix(n, src, dst)

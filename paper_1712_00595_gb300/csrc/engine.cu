@@ -72,6 +72,7 @@ struct osp_ctx {
   bool loaded = false, seeded = false, scored = false;
   int seed = -1;
   int S = 1;                   // seeds tracked (S > 1: the seed block d.mu)
+  int64_t pagerank_n = 0;      // > 0: uniform restart vector over nodes 0..pagerank_n-1
   double c = 0.15;
   int grid_multi = 0;
   int grid_multi_init = 0;
@@ -1008,17 +1009,18 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
   if (!seeds || S < 1 || S > kMaxSeeds)
     return fail(ctx, OSP_EINVAL, "need between 1 and 256 seeds");
   if (!(c > 0.0 && c < 1.0)) return fail(ctx, OSP_EINVAL, "c must lie in (0, 1)");
+  const bool pagerank = S == 1 && seeds[0] == OSP_PAGERANK;
   std::vector<int32_t> sorted(seeds, seeds + S);
   std::sort(sorted.begin(), sorted.end());
-  for (int i = 0; i < S; ++i) {
+  for (int i = 0; i < S && !pagerank; ++i) {
     if (sorted[i] < 0 || sorted[i] >= ctx->n) return fail(ctx, OSP_EINVAL, "seed id out of range");
     if (i > 0 && sorted[i] == sorted[i - 1]) return fail(ctx, OSP_EINVAL, "duplicate seed");
   }
   if (S == 1 && ctx->opt.precision == OSP_PREC_BF16_ACC64)
     return fail(ctx, OSP_ENOTSUP, "bf16 gather vectors are built for two or more seeds");
   CK(cudaSetDevice(ctx->device));
-  std::vector<int32_t> s_int(S);
-  for (int i = 0; i < S; ++i) {
+  std::vector<int32_t> s_int(S, 0);
+  for (int i = 0; i < S && !pagerank; ++i) {
     s_int[i] = ctx->e2i[seeds[i]];
     unsigned char dead = 0;
     CK(cudaMemcpy(&dead, ctx->d.dead + s_int[i], 1, cudaMemcpyDeviceToHost));
@@ -1030,15 +1032,17 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
   Ctl h;
   osp_status s = read_ctl(ctx, &h);
   if (s != OSP_OK) return s;
-  h.seed = s_int[0];
+  h.seed = pagerank ? -1 : s_int[0];
   h.c = c;
   h.multi = S > 1;
+  ctx->pagerank_n = pagerank ? ctx->n : 0;
   s = write_ctl(ctx, h);
   if (s != OSP_OK) return s;
   ctx->seed = seeds[0];
   ctx->c = c;
   CK(cudaMemsetAsync(ctx->d.seedflag, 0, ctx->nc, ctx->stream));
-  for (int i = 0; i < S; ++i) CK(cudaMemsetAsync(ctx->d.seedflag + s_int[i], 1, 1, ctx->stream));
+  for (int i = 0; i < S && !pagerank; ++i)
+    CK(cudaMemsetAsync(ctx->d.seedflag + s_int[i], 1, 1, ctx->stream));
   k_set_scale<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->d, (int)ctx->n, c);
   ++ctx->launches;
   CK(cudaGetLastError());
@@ -1107,7 +1111,10 @@ osp_status enqueue_cpi_start(osp_ctx* ctx) {
     k_multi_cpi_begin<<<1, kMaxSeeds, 0, ctx->stream>>>(ctx->d);
   } else {
     CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
-    k_cpi_begin<<<1, 1, 0, ctx->stream>>>(ctx->d);
+    if (ctx->pagerank_n > 0)
+      k_cpi_begin_uniform<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->d, (int)ctx->pagerank_n);
+    else
+      k_cpi_begin<<<1, 1, 0, ctx->stream>>>(ctx->d);
   }
   ++ctx->launches;
   CK(cudaGetLastError());

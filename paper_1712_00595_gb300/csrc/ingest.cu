@@ -190,6 +190,16 @@ __global__ void k_reset_batch(Dev d, int cont) {
 }
 
 // CPI start (Sec. 2.2): x(0) = c e_s, r = 0 before the propagation adds x(0).
+// CPI start with the uniform restart vector q = 1/n0 over nodes 0..n0-1
+// (PageRank mode): x(0) = c q, collected by the dense x(0) scan.
+__global__ void k_cpi_begin_uniform(Dev d, int n0) {
+  Ctl* c = d.ctl;
+  const double x = c->c / (double)n0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n0; v += gridDim.x * blockDim.x)
+    d.xacc[v] = x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->dense0 = 1;
+}
+
 __global__ void k_cpi_begin(Dev d) {
   Ctl* c = d.ctl;
   int s = c->seed;

@@ -6,6 +6,7 @@ namespace osp {
 
 __global__ void k_reset_batch(Dev d, int cont);
 __global__ void k_cpi_begin(Dev d);
+__global__ void k_cpi_begin_uniform(Dev d, int n0);
 __global__ void k_ingest(Dev d, const osp_update* __restrict__ ops, int U);
 __global__ void k_expand(Dev d);
 __global__ void k_merge_pieces(Dev d, double beta);

@@ -294,6 +294,40 @@ def test_large_batch_in_sub_batches():
     eng.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_pagerank_mode_uniform_restart(prec):
+    """seed = OSP_PAGERANK: q uniform over the nodes at osp_set_seeds, fixed
+    afterwards. CPI and OSP through all op kinds match the oracle run from
+    x(0) = c q; at the end, a recompute on the final graph with the same q."""
+    rng = np.random.default_rng(90 + prec)
+    n = 500
+    src, dst = hub_graph(rng, n=n, m=4000, hub_in=400, hub_out=250, mids=5)
+    batches = mixed_sequence(rng, n, src, dst, 4, 120)
+    eps = 1e-12
+    eng = N.Engine(precision=prec, device=0, max_nodes=n + 4096)
+    eng.load_graph(n, src, dst)
+    eng.set_seeds([-1], C_RESTART)
+    st = eng.init_scores(eps)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    force = st["iterations"] if prec == N.OSP_PREC_FP32_ACC64 else 0
+    r_o, _, _ = O.propagate(*cur, np.full(n, C_RESTART / n), C_RESTART, eps, force_iters=force)
+    assert l1(eng.query(), r_o) <= TOL[prec]
+    for ops in batches:
+        st = eng.apply_updates(ops, eps)
+        assert g.apply(ops) == -1
+        new = g.csr()
+        force = st["iterations"] if prec == N.OSP_PREC_FP32_ACC64 else 0
+        r_o, _, _, _ = O.osp(cur, new, r_o, C_RESTART, eps, force_iters=force)
+        cur = new
+        assert l1(eng.query(), r_o) <= TOL[prec]
+    q = np.zeros(g.n)
+    q[:n] = 1.0 / n
+    r_cpi, _, _ = O.propagate(*cur, C_RESTART * q, C_RESTART, 1e-14)
+    assert l1(eng.query(), r_cpi) <= TOL[prec] + 1e-9
+    eng.close()
+
+
 def test_invalid_batches_rejected_state_unchanged():
     rng = np.random.default_rng(9)
     n = 50

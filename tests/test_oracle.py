@@ -440,3 +440,36 @@ def test_generators_are_seeded_and_valid():
         assert not es.contains(W.edge_keys(ins["u"], ins["v"])).any()
         assert es.contains(W.edge_keys(dels["u"], dels["v"])).all()
         es.apply(W.edge_keys(ins["u"], ins["v"]), W.edge_keys(dels["u"], dels["v"]))
+
+
+def test_uniform_restart_vector_pagerank_mode():
+    """PageRank mode (uniform q): on a directed cycle every node keeps 1/n (A~ 1 =
+    1 so r = c (1 - (1-c))^-1 q); on random graphs with dead-ends the CPI series
+    from x(0) = c q matches the dense solve of Eq. 1 with that q."""
+    n, c = 9, 0.15
+    src = np.arange(n, dtype=np.int32)
+    dst = ((src + 1) % n).astype(np.int32)
+    g = O.Graph(n, src, dst)
+    r, _, _ = O.propagate(*g.csr(), np.full(n, c / n), c, 1e-15)
+    assert np.allclose(r, 1.0 / n, rtol=0, atol=1e-13)
+    rng = np.random.default_rng(12)
+    for _ in range(3):
+        n = 60
+        src = rng.integers(0, n, 200).astype(np.int32)
+        dst = rng.integers(0, n, 200).astype(np.int32)
+        src[src < 5] = 5  # nodes 0..4 keep no out-edges (dead-ends)
+        g = O.Graph(n, src, dst)
+        q = np.full(n, 1.0 / n)
+        r, _, _ = O.propagate(*g.csr(), c * q, c, 1e-15)
+        want = O.dense_rwr_q(n, *O_edges(g), q, c)
+        assert np.abs(r - want).sum() <= 1e-12
+        # the seed form is the special case q = e_s
+        e = np.zeros(n)
+        e[7] = 1.0
+        assert np.abs(O.dense_rwr_q(n, *O_edges(g), e, c) - O.dense_rwr(n, *O_edges(g), 7, c)).sum() <= 1e-14
+
+
+def O_edges(g):
+    rp, col = g.csr()
+    src = np.repeat(np.arange(rp.size - 1), np.diff(rp)).astype(np.int32)
+    return src, np.asarray(col, np.int32)
