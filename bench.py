@@ -76,7 +76,7 @@ def parse():
     p.add_argument("--launch", default="graphs", choices=["graphs", "eager"],
                    help="batch kernels replayed from CUDA graphs, or launched one by one")
     p.add_argument("--workload", default="rmat20",
-                   choices=["rmat20", "serve22"] + sorted(MULTI_WORKLOADS),
+                   choices=["rmat20", "serve22", "location", "growshrink"] + sorted(MULTI_WORKLOADS),
                    help="rmat20: the one-seed headline; the others track many seeds at once")
     p.add_argument("--serve-policy", default="latest", choices=["ordered", "latest"],
                    help="serve22: queries read in arrival order, or the newest scores")
@@ -703,6 +703,102 @@ def run_serve(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+def run_location(args, rank, world):
+    """Cost of one update against the score of the node it touches (Sec. 3.3:
+    ||q_offset||_1 <= (1-c) r[u] times 2): nodes with out-edges are ranked by
+    their score into 100 buckets and 10 nodes per bucket each lose one
+    out-edge, one batch per deletion (exact mode, eps = 1e-9)."""
+    import torch
+
+    from paper_1712_00595_gb300 import native as N
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, src, dst, seed, _ = make_workload(args.scale, 1)
+    eng = N.Engine(precision=N.OSP_PREC_FP32_ACC64, use_graphs=True)
+    eng.load_graph(n, src, dst)
+    eng.set_seeds([seed], C_RESTART)
+    eng.init_scores(1e-10)
+    r = eng.query()
+    ptr, idx = eng.export_graph(0)
+    outdeg = np.diff(ptr)
+    cand = np.flatnonzero(outdeg > 0)
+    cand = cand[np.lexsort((cand, -r[cand]))]
+    rng = W.rng_for(W.BASE_SEED + 11)
+    rows = []
+    for b, part in enumerate(np.array_split(cand, 100)):
+        pick = rng.choice(part, min(10, part.size), replace=False)
+        ms, it, q = [], [], []
+        for u in pick:
+            v = idx[ptr[u] + int(rng.integers(0, outdeg[u]))]
+            ops = np.zeros(1, W.UPDATE_DTYPE)
+            ops["u"], ops["v"], ops["op"] = u, v, W.OP_DELETE_EDGE
+            st = eng.apply_updates(ops, 1e-9)
+            ms.append(st["ms_update"] + st["ms_propagate"])
+            it.append(st["iterations"])
+            q.append(st["qoff_l1"])
+            outdeg[u] = 0  # one deletion per node
+        rows.append({"bucket": b, "score_mean": float(r[pick].mean()), "ms_mean": float(np.mean(ms)),
+                     "iterations_mean": float(np.mean(it)), "qoff_l1_mean": float(np.mean(q))})
+    eng.close()
+    ms = np.array([x["ms_mean"] for x in rows])
+    out = {"metric": "one-edge update cost by score bucket of its source (exact OSP, eps 1e-9)",
+           "value": float(ms[:10].mean() / ms[-10:].mean()), "unit": "cost ratio, top 10 vs bottom 10 buckets",
+           "n_gpus": world, "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "location_sweep_rmat%d" % args.scale, "buckets": 100, "per_bucket": 10},
+           "buckets": rows}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_growshrink(args, rank, world):
+    """Cost of a fixed-size batch (1,000 edges) against the graph size: the
+    graph grows from half of its edges to all of them in 32 steps and then
+    shrinks back; each step applies one measured 1,000-edge batch (insertions
+    while growing, deletions while shrinking) and then the rest of its 1/32
+    share as one large untimed batch (OSP-T, eps = 1e-6)."""
+    import torch
+
+    from paper_1712_00595_gb300 import native as N
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    gen, src, dst = W.rmat_graph(args.scale, 16 << args.scale, seed=W.BASE_SEED + HUB_SEED_OFFSET)
+    n = gen.n
+    seed = W.max_out_degree_seed(n, src)
+    order = W.rng_for(W.BASE_SEED + 12).permutation(src.size)
+    half = src.size // 2
+    base, extra = order[:half], order[half:]
+    eng = N.Engine(precision=N.OSP_PREC_FP32_ACC64, use_graphs=True)
+    eng.load_graph(n, src[base], dst[base])
+    eng.set_seeds([seed], C_RESTART)
+    eng.init_scores(1e-10)
+    steps = 32
+    chunk = extra.size // steps
+    rows = []
+
+    def batch(sel, op):
+        ops = np.zeros(sel.size, W.UPDATE_DTYPE)
+        ops["u"], ops["v"], ops["op"] = src[sel], dst[sel], op
+        return eng.apply_updates(ops, 1e-6)
+
+    for phase in ("grow", "shrink"):
+        op = W.OP_INSERT_EDGE if phase == "grow" else W.OP_DELETE_EDGE
+        for k in range(steps):
+            part = extra[k * chunk:(k + 1) * chunk]
+            st = batch(part[:1000], op)  # the measured batch of fixed size
+            rows.append({"phase": phase, "m": int(st["m_edges"]), "iterations": int(st["iterations"]),
+                         "ms": float(st["ms_update"] + st["ms_propagate"]),
+                         "qoff_l1": float(st["qoff_l1"])})
+            batch(part[1000:], op)  # the rest of the chunk: the graph moves on
+    eng.close()
+    out = {"metric": "update cost as the graph grows and shrinks (1,000-edge batches, eps 1e-6)",
+           "value": float(np.mean([x["ms"] for x in rows])), "unit": "ms per batch (mean)",
+           "n_gpus": world, "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "growshrink_rmat%d" % args.scale, "batches_per_phase": steps},
+           "batches": rows}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -710,6 +806,10 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "serve22":
         run_serve(args, rank, world)
+    elif args.workload == "location":
+        run_location(args, rank, world)
+    elif args.workload == "growshrink":
+        run_growshrink(args, rank, world)
     elif args.workload != "rmat20":
         run_multi(args, rank, world)
     else:
