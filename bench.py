@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU time bound of the cpu_baseline sample (whole batches)")
+    p.add_argument("--node-order", type=int, default=0, choices=[0, 1],
+                   help="internal node order: 0 = caller ids, 1 = descending out-degree")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default pull-step schedule (osp_init_scores tunes it otherwise)")
     p.add_argument("--launch", default="graphs", choices=["graphs", "eager"],
@@ -363,7 +365,7 @@ def run_ours(args, rank, world):
 
     def new_engine(prec, graphs=args.launch == "graphs"):
         e = N.Engine(precision=prec, device=local, stream=tstream.cuda_stream, use_graphs=graphs,
-                     autotune=args.autotune)
+                     autotune=args.autotune, node_order=args.node_order)
         e.load_graph(n, src, dst)
         e.set_seeds([seed], C_RESTART)
         e.init_scores(args.eps_init)

@@ -337,15 +337,19 @@ __global__ void k_pull_plan(Dev d, int hub_thr, int node_w, int task_items) {
     ctl->n_tasks = nt;
     ctl->hub_thr = hub_thr;
   }
-  for (int t = tid; t <= nt; t += nth) {
-    const long long target = (long long)t * task_items;
-    int lo = 0, hi = n;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((long long)d.pc[mid] + (long long)node_w * mid < target) lo = mid + 1;
-      else hi = mid;
-    }
-    d.task_first[t] = t == nt ? n : lo;
+  // f(v) = pc[v] + node_w v is nondecreasing with f(0) = 0, so the tasks t with
+  // f(v-1) < t * task_items <= f(v) are exactly those starting at node v: one
+  // coalesced pass over the nodes writes every task start.
+  if (tid == 0) {
+    d.task_first[0] = 0;
+    d.task_first[nt] = n;
+  }
+  for (int v = tid + 1; v <= n; v += nth) {
+    const long long f0 = (long long)d.pc[v - 1] + (long long)node_w * (v - 1);
+    const long long f1 = (long long)d.pc[v] + (long long)node_w * v;
+    const long long t0 = f0 / task_items + 1;
+    const long long t1 = min(f1 / task_items, (long long)nt - 1);
+    for (long long t = t0; t <= t1; ++t) d.task_first[t] = v;
   }
   const int lane = threadIdx.x & 31;
   __shared__ unsigned long long s_cnt[2];

@@ -464,22 +464,37 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
       // The merge reached more than n/beta nodes and queued none of them: one
       // coalesced pass over all nodes collects x(0) (xacc is zero off its
       // support) and builds the frontier queue of its nonzero entries.
-      // One queue reservation per CTA tile of blockDim.x nodes (the loop is
-      // uniform over the CTA).
+      // One queue reservation per CTA tile of 4 x blockDim.x nodes, whose x
+      // values load together (the loop is uniform over the CTA).
       const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-      for (int base = blockIdx.x * blockDim.x; base < n; base += nthreads) {
-        const int v = base + threadIdx.x;
-        const double x = v < n ? __ldcg(d.xacc + v) : 0.0;
-        const bool nz = x != 0.0;
-        if (nz) {
-          d.xacc[v] = 0.0;
-          d.r[v] += x;
-          l1 += fabs(x);
-          yb[0][v] = (T)(x * __ldg(d.scale_d + v));
-          ef += __ldg(d.len_r + v);
+      for (int base = blockIdx.x * 4 * blockDim.x; base < n; base += 4 * nthreads) {
+        double xs[4];
+        int vs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          vs[k] = base + k * blockDim.x + threadIdx.x;
+          xs[k] = vs[k] < n ? __ldcg(d.xacc + vs[k]) : 0.0;
         }
-        const unsigned b = __ballot_sync(0xffffffffu, nz);
-        if (lane == 0) s_qw[w] = __popc(b);
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (xs[k] != 0.0) {
+            const int v = vs[k];
+            d.xacc[v] = 0.0;
+            d.r[v] += xs[k];
+            l1 += fabs(xs[k]);
+            yb[0][v] = (T)(xs[k] * __ldg(d.scale_d + v));
+            ef += __ldg(d.len_r + v);
+            ++cnt;
+          }
+        }
+        int inc = cnt;  // inclusive warp scan of the counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_qw[w] = inc;
         __syncthreads();
         if (threadIdx.x == 0) {
           int t = 0;
@@ -491,7 +506,10 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
           s_qbase = t ? atomicAdd(&ctl->q_size[0], t) : 0;
         }
         __syncthreads();
-        if (nz) d.q0[s_qbase + s_qw[w] + __popc(b & lanemask_lt())] = v;
+        int pos = s_qbase + s_qw[w] + inc - cnt;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (xs[k] != 0.0) d.q0[pos++] = vs[k];
         __syncthreads();
       }
     } else {
