@@ -282,7 +282,8 @@ def run_reference(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, n, len(src), seed, "fp64 (CPU oracle)"),
+        "config": dict(workload_config(args, n, len(src), seed, "fp64 (CPU oracle)"),
+                       l2="n/a (host)", inputs="update batches in host memory"),
         "cpu_baseline": {"value": v, "unit": "batches/s", "cores": 1, "kind": "oracle",
                          "sample": "%d batches of the workload, single-threaded C oracle" % args.steps},
         "e2e": {"value": v, "unit": "batches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -306,7 +306,12 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
     int v = (int)((key >> 14) & 0x1FFFFFF);
     bool present_after = ops[p].op == OSP_OP_INSERT_EDGE;
     bool present_before = false;
-    if (u < n_old) present_before = contains_i(d.pool_r + d.off_r[u], d.len_r[u], v);
+    if (u < n_old && v < n_old) {
+      // u -> v exists iff v is in u's out-list, or u in v's in-list: search the shorter
+      const int lr = d.len_r[u], lc = d.len_c[v];
+      present_before = lr <= lc ? contains_i(d.pool_r + d.off_r[u], lr, v)
+                                : contains_i(d.pool_c + d.off_c[v], lc, u);
+    }
     if (present_after && !present_before) fb |= 1u << (2 * k);
     if (!present_after && present_before) fb |= 2u << (2 * k);
   }
