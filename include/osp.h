@@ -71,6 +71,12 @@ typedef enum {
  *                            score 0; u and v are ignored.
  *  OSP_OP_DELETE_NODE (u):   remove every out- and in-edge of u; the id stays
  *                            allocated and dead and may not be named again.
+ *  OSP_OP_ZERO_ROW (u):      the literal form of the node deletion of Sec. 3.4.1:
+ *                            only u's row of B~ becomes zero, i.e. every out-edge
+ *                            of u is removed (u turns into a dead-end); its
+ *                            in-edges stay, u stays live and later ops may name
+ *                            it again (an edge u->v inserted after the op is
+ *                            kept). Allowed on a seed. v is ignored.
  * A batch is invalid if an op names an id that does not exist at that point
  * of the batch or is dead, deletes a node twice, deletes a seed, or has an
  * unknown op code. */
@@ -78,7 +84,8 @@ enum {
     OSP_OP_INSERT_EDGE = 0,
     OSP_OP_DELETE_EDGE = 1,
     OSP_OP_ADD_NODE = 2,
-    OSP_OP_DELETE_NODE = 3
+    OSP_OP_DELETE_NODE = 3,
+    OSP_OP_ZERO_ROW = 4
 };
 typedef struct {
     int32_t u;

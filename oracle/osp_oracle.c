@@ -26,7 +26,9 @@
  *  - Node insertion (Sec. 3.4.1): a new node gets the next id, an empty row
  *    and column, and a zero score. Node deletion removes the node's out-edges
  *    (its row of B~ becomes zero) and also its in-edges; its id is never
- *    reused.
+ *    reused. Op 4 is the literal form of that sentence: only the node's row
+ *    becomes zero (all its out-edges go); its in-edges stay and the node
+ *    stays live.
  *  - Update batches: operations apply in order; Delta A is the difference
  *    between the rows after the whole batch and the rows before it.
  */
@@ -36,7 +38,8 @@
 #include <string.h>
 
 typedef struct {
-    int32_t u, v, op; /* op: 0 insert edge, 1 delete edge, 2 add node, 3 delete node */
+    int32_t u, v, op; /* op: 0 insert edge, 1 delete edge, 2 add node, 3 delete node,
+                         4 zero the node's row (remove its out-edges only) */
 } orc_update;
 
 typedef struct {
@@ -212,7 +215,7 @@ int64_t orc_graph_m(const orc_graph *g) { return g->m; }
 
 /* Check a batch against the sequential rules without changing the graph.
  * Returns -1 if valid, else the index of the first invalid operation.
- * Rules: op codes 0..3; every id named must exist at that point of the batch
+ * Rules: op codes 0..4; every id named must exist at that point of the batch
  * (nodes added earlier in the batch count) and must not have been deleted
  * before (earlier batches or earlier in this batch); a node is deleted at
  * most once and never if it is in protect[0..n_protect). */
@@ -236,6 +239,8 @@ int64_t orc_graph_validate(const orc_graph *g, const orc_update *ops, int64_t U,
             for (int32_t s = 0; s < n_protect && bad < 0; s++)
                 if (protect[s] == u) bad = p;
             if (bad < 0) dead[u] = 1;
+        } else if (op == 4) {
+            if (u < 0 || u >= n || dead[u]) bad = p;
         } else {
             bad = p;
         }
@@ -267,6 +272,13 @@ int64_t orc_graph_apply(orc_graph *g, const orc_update *ops, int64_t U, const in
         } else if (op == 2) { /* add node: next id, empty row and column */
             if (graph_grow(g, g->n + 1)) return -2;
             g->n++;
+        } else if (op == 4) { /* zero row u: its out-edges go, nothing else changes */
+            ivec *o = &g->out[u];
+            for (int32_t t = 0; t < o->len; t++) {
+                ivec_remove(&g->in[o->a[t]], u);
+                g->m--;
+            }
+            o->len = 0;
         } else { /* delete node u: all out- and in-edges go, the id stays dead */
             ivec *o = &g->out[u];
             for (int32_t t = 0; t < o->len; t++) {

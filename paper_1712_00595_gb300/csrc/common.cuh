@@ -50,6 +50,7 @@ struct Ctl {
   long long net_ins, net_del;  // edge edits of the batch (node deletions not included)
   int n_rec_r, n_rec_c;        // changed row / column records
   int n_del;                   // nodes deleted by the batch
+  int n_clr;                   // rows zeroed by the last ingested batch (clr_nodes)
   int n_hubs, n_pieces;        // pull step: long in-lists and their pieces
   int n_tasks;                 // pull step: warp tasks
   int n_mpieces;               // merge pieces of the current batch
@@ -114,6 +115,7 @@ struct Dev {
   unsigned char* dead;
   unsigned char* seedflag;  // 1 for the seed node(s): they cannot be deleted
   int* del_pos;        // first deletion position in the batch (kNoPos if none)
+  int* clr_pos;        // last OSP_OP_ZERO_ROW position of the last batch (-1 if none)
   int* rflag; int* cflag;
   // batch scratch: net edits grouped per changed row / column
   int* ins_r; int* del_r; int* ins_c; int* del_c;   // [kMaxBatch]
@@ -121,6 +123,7 @@ struct Dev {
   int* rec_r_node; int* rec_r_is; int* rec_r_ic; int* rec_r_ds; int* rec_r_dc;  // [nc]
   int* rec_c_node; int* rec_c_is; int* rec_c_ic; int* rec_c_ds; int* rec_c_dc;  // [nc]
   int* del_nodes;  // [kMaxBatch]
+  int* clr_nodes;  // [kMaxBatch] rows zeroed by the last ingested batch
   // merge plan over the changed lists (out-lists first, then in-lists)
   unsigned* rec_old_off; int* rec_old_len; int* rec_pstart;  // [2 nc + 1]
   unsigned* rec_fbase; int* rec_dp;                          // [2 nc]

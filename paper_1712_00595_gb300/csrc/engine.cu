@@ -911,6 +911,7 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(d.dead, nc, 0);
   AL(d.seedflag, nc, 0);
   AL(d.del_pos, nc, 0x7F);
+  AL(d.clr_pos, nc, 0xFF);
   AL(d.rflag, nc, 0);
   AL(d.cflag, nc, 0);
   AL(d.ins_r, kMaxBatch, 0);
@@ -930,6 +931,7 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(d.rec_c_ds, nc, 0);
   AL(d.rec_c_dc, nc, 0);
   AL(d.del_nodes, kMaxBatch, 0);
+  AL(d.clr_nodes, kMaxBatch, 0);
   AL(d.rec_old_off, 2 * nc + 1, 0);
   AL(d.rec_old_len, 2 * nc + 1, 0);
   AL(d.rec_pstart, 2 * nc + 1, 0);

@@ -212,15 +212,21 @@ __global__ void k_cpi_begin(Dev d) {
 __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_update* __restrict__ ops,
                                                            int U) {
   extern __shared__ unsigned long long skey[];
-  __shared__ int s_bad, s_ndel;
+  __shared__ int s_bad, s_ndel, s_nclr;
+  __shared__ long long s_reins;
   __shared__ unsigned s_flags[kIngestThreads];
   Ctl* ctl = d.ctl;
   if (U < 0) U = ctl->batch_U;  // replayed from a CUDA graph: the size is set per call
   const int tid = threadIdx.x;
   const int n_old = ctl->n;
+  // rows zeroed by the previous batch (merged by now) lose their mark
+  const int n_clr_prev = ctl->n_clr;
+  for (int i = tid; i < n_clr_prev; i += kIngestThreads) d.clr_pos[d.clr_nodes[i]] = -1;
   if (tid == 0) {
     s_bad = kNoPos;
     s_ndel = 0;
+    s_nclr = 0;
+    s_reins = 0;
   }
   __syncthreads();
 
@@ -241,6 +247,10 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       const int w = o.u;
       if (w >= 0 && w < na && !d.dead[w] && !d.seedflag[w]) atomicMin(&d.del_pos[w], p);
       else atomicMin(&s_bad, p);
+    } else if (o.op == OSP_OP_ZERO_ROW) {
+      // the last zeroing of a row in the batch voids the row's earlier edge ops
+      if (o.u >= 0 && o.u < n_old + run) atomicMax(&d.clr_pos[o.u], p);
+      else atomicMin(&s_bad, p);
     }
   }
   __syncthreads();
@@ -257,6 +267,8 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       ++run;
     } else if (o.op == OSP_OP_DELETE_NODE) {
       ok = o.u >= 0 && o.u < na && !d.dead[o.u] && !d.seedflag[o.u] && d.del_pos[o.u] == p;
+    } else if (o.op == OSP_OP_ZERO_ROW) {
+      ok = o.u >= 0 && o.u < na && !d.dead[o.u] && d.del_pos[o.u] > p;
     } else {
       ok = false;
     }
@@ -264,14 +276,20 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   }
   __syncthreads();
   if (s_bad != kNoPos) {
-    for (int p = lo; p < hi; ++p)
-      if (ops[p].op == OSP_OP_DELETE_NODE) {
+    for (int p = lo; p < hi; ++p) {
+      const int op = ops[p].op;
+      if (op == OSP_OP_DELETE_NODE || op == OSP_OP_ZERO_ROW) {
         const osp_update o = load_op(ops, p, d);
-        if (o.u >= 0 && o.u < d.nc) d.del_pos[o.u] = kNoPos;
+        if (o.u >= 0 && o.u < d.nc) {
+          if (op == OSP_OP_DELETE_NODE) d.del_pos[o.u] = kNoPos;
+          else d.clr_pos[o.u] = -1;
+        }
       }
+    }
     if (tid == 0) {
       ctl->status = OSP_EINVAL;
       ctl->bad_op = s_bad;
+      ctl->n_clr = 0;
     }
     return;
   }
@@ -282,7 +300,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
     osp_update o = load_op(ops, p, d);
     unsigned long long key = kNoKey;
     if ((o.op == OSP_OP_INSERT_EDGE || o.op == OSP_OP_DELETE_EDGE) && d.del_pos[o.u] == kNoPos &&
-        d.del_pos[o.v] == kNoPos)
+        d.del_pos[o.v] == kNoPos && d.clr_pos[o.u] < p)
       key = ((unsigned long long)o.u << 39) | ((unsigned long long)o.v << 14) | (unsigned)p;
     skey[p] = key;
   }
@@ -294,6 +312,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   const int per = max(1, N / kIngestThreads);
   const int pi0 = tid * per;
   unsigned fb = 0;
+  int reins = 0;
   for (int k = 0; k < per; ++k) {
     int i = pi0 + k;
     if (i >= N) break;
@@ -312,19 +331,27 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       present_before = lr <= lc ? contains_i(d.pool_r + d.off_r[u], lr, v)
                                 : contains_i(d.pool_c + d.off_c[v], lc, u);
     }
+    if (d.clr_pos[u] >= 0) {
+      // u's row was zeroed before this op: the merge drops every old entry of
+      // the row (and u from the old in-lists), so a surviving edge is written
+      // again as an insertion, but it is not a new edge
+      reins += present_after && present_before;
+      present_before = false;
+    }
     if (present_after && !present_before) fb |= 1u << (2 * k);
     if (!present_after && present_before) fb |= 2u << (2 * k);
   }
   s_flags[tid] = fb;
+  if (reins) atomicAdd((unsigned long long*)&s_reins, (unsigned long long)reins);
   long long n_ins = 0, n_del = 0;
   emit_groups(
       skey, N, per, pi0, &s_flags[tid], [](unsigned long long k) { return (int)(k >> 39); },
       [](unsigned long long k) { return (int)((k >> 14) & 0x1FFFFFF); }, d.ins_r, d.del_r, d.gi,
       d.gd, d.rec_r_node, d.rec_r_is, d.rec_r_ic, d.rec_r_ds, d.rec_r_dc, d.rflag, &ctl->n_rec_r,
       &n_ins, &n_del);
-  if (tid == 0) {
-    ctl->net_ins = n_ins;
-    ctl->net_del = n_del;
+  if (tid == 0) {  // summed over the sub-batches of a large batch
+    ctl->net_ins += n_ins - s_reins;
+    ctl->net_del += n_del;
   }
 
   // ---- the same edits keyed (v, u) for the in-lists ----
@@ -366,19 +393,27 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       &c_del);
 
   // ---- node deletions and additions ----
-  for (int p = lo; p < hi; ++p)
+  for (int p = lo; p < hi; ++p) {
     if (ops[p].op == OSP_OP_DELETE_NODE) d.del_nodes[atomicAdd(&s_ndel, 1)] = load_op(ops, p, d).u;
+    if (ops[p].op == OSP_OP_ZERO_ROW) {
+      const int u = load_op(ops, p, d).u;
+      if (d.clr_pos[u] == p) d.clr_nodes[atomicAdd(&s_nclr, 1)] = u;  // once per row
+    }
+  }
   __syncthreads();
   for (int p = lo; p < hi; ++p)
     if (ops[p].op == OSP_OP_DELETE_NODE) d.del_pos[load_op(ops, p, d).u] = kNoPos;
   if (tid == 0) {
     ctl->n_del = s_ndel;
+    ctl->n_clr = s_nclr;
     ctl->n = n_old + tot_adds;
   }
 }
 
 // Node deletions: the deleted node's own row and column are cleared, and every
-// row / column holding it as a neighbour is re-written without it.
+// row / column holding it as a neighbour is re-written without it. A zeroed
+// row (OSP_OP_ZERO_ROW) is re-written empty but for its insertions after the
+// op, and so is every in-list holding it.
 __global__ void k_expand(Dev d) {
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
@@ -421,6 +456,26 @@ __global__ void k_expand(Dev d) {
         int at = atomicAdd(&ctl->n_rec_r, 1);
         d.rec_r_node[at] = x;
         d.rec_r_is[at] = d.rec_r_ic[at] = d.rec_r_ds[at] = d.rec_r_dc[at] = 0;
+      }
+    }
+  }
+  const int nz = ctl->n_clr;
+  for (int k = gw; k < nz; k += nw) {
+    const int w = d.clr_nodes[k];
+    if (lane == 0 && atomicExch(&d.rflag[w], 1) == 0) {
+      int at = atomicAdd(&ctl->n_rec_r, 1);
+      d.rec_r_node[at] = w;
+      d.rec_r_is[at] = d.rec_r_ic[at] = d.rec_r_ds[at] = d.rec_r_dc[at] = 0;
+    }
+    // old out-neighbours x of w: column x loses source w (re-inserted if kept)
+    const unsigned orow = d.off_r[w];
+    const int lrow = d.len_r[w];
+    for (int j = lane; j < lrow; j += 32) {
+      int x = d.pool_r[orow + j];
+      if (atomicExch(&d.cflag[x], 1) == 0) {
+        int at = atomicAdd(&ctl->n_rec_c, 1);
+        d.rec_c_node[at] = x;
+        d.rec_c_is[at] = d.rec_c_ic[at] = d.rec_c_ds[at] = d.rec_c_dc[at] = 0;
       }
     }
   }

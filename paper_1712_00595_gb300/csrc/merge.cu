@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
   const bool queue = !ctl->dense0;
   const bool multi = ctl->multi;
   const bool any_dead = ctl->n_del > 0;  // only nodes deleted by this batch still have edges
+  const bool any_clr = ctl->n_clr > 0;   // rows zeroed by this batch
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -150,7 +151,9 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
     const int q = p - d.rec_pstart[c];
     const unsigned o = d.rec_old_off[c];
     const int L = d.rec_old_len[c];
-    const bool cleared = any_dead && d.dead[R.node];
+    const bool cleared =
+        (any_dead && d.dead[R.node]) || (any_clr && R.rows && d.clr_pos[R.node] >= 0);
+    const bool drop_clr = any_clr && !R.rows;  // in-lists drop sources whose row was zeroed
     const double ru = R.rows && !multi ? d.r[R.node] : 0.0;  // the seed block has its own offset kernel
     const bool contrib = R.rows && ru != 0.0;
     const double wa = L ? 1.0 / (double)L : 0.0;
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(256) k_merge_count(Dev d) {
       int a = in ? R.pool[o + i] : 0;
       if (in && !OSP_GUARD(d.ctl, a >= 0 && a < d.nc, "merge count entry", c, i, a)) a = 0;
       const bool keep = in && !cleared && !(any_dead && d.dead[a]) &&
-                        !contains_i(R.del + R.ds, R.dc, a);
+                        !(drop_clr && d.clr_pos[a] >= 0) && !contains_i(R.del + R.ds, R.dc, a);
       cnt += __popc(__ballot_sync(0xffffffffu, keep));
       if (contrib) offset_add(d, in && !keep, a, c1 * ru * (0.0 - wa), epoch, queue);
     }
@@ -238,6 +241,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
   const bool queue = !ctl->dense0;
   const bool multi = ctl->multi;
   const bool any_dead = ctl->n_del > 0;
+  const bool any_clr = ctl->n_clr > 0;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -253,7 +257,9 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
     const int base = d.piece_base[p];
     const int* I = R.ins + R.is;
     const int ic = R.ic;
-    const bool cleared = any_dead && d.dead[R.node];
+    const bool cleared =
+        (any_dead && d.dead[R.node]) || (any_clr && R.rows && d.clr_pos[R.node] >= 0);
+    const bool drop_clr = any_clr && !R.rows;  // in-lists drop sources whose row was zeroed
     const double ru = R.rows && !multi ? d.r[R.node] : 0.0;  // the seed block has its own offset kernel
     const bool contrib = R.rows && ru != 0.0;
     const double wa = L ? 1.0 / (double)L : 0.0;
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(256) k_merge_write(Dev d) {
       int a = in ? R.pool[o + i] : 0;
       if (in && !OSP_GUARD(d.ctl, a >= 0 && a < d.nc, "merge write entry", c, i, a)) a = 0;
       const bool keep = in && !cleared && !(any_dead && d.dead[a]) &&
-                        !contains_i(R.del + R.ds, R.dc, a);
+                        !(drop_clr && d.clr_pos[a] >= 0) && !contains_i(R.del + R.ds, R.dc, a);
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       masks[r] = m;
       if (keep) {

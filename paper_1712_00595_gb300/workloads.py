@@ -25,6 +25,7 @@ OP_INSERT_EDGE = 0
 OP_DELETE_EDGE = 1
 OP_ADD_NODE = 2
 OP_DELETE_NODE = 3
+OP_ZERO_ROW = 4
 
 BASE_SEED = 20180423
 
@@ -257,11 +258,12 @@ def edge_update_stream(src, dst, n: int, batches: int, n_ins: int, n_del: int, s
 
 
 def random_mixed_batch(rng, n: int, es: EdgeSet, dead: np.ndarray, n_ops: int,
-                       p_add=0.05, p_delnode=0.03, protect=()):
-    """A small batch mixing all four op kinds, valid in sequence (used by tests).
+                       p_add=0.05, p_delnode=0.03, protect=(), p_zero_row=0.0):
+    """A small batch mixing the op kinds, valid in sequence (used by tests).
 
     Node deletions never hit ``protect`` (the seeds) and later ops never name
-    a node deleted earlier. ``dead`` is updated in place; the returned n is the
+    a node deleted earlier. ``p_zero_row`` > 0 adds row zeroings (any live
+    node, seeds included). ``dead`` is updated in place; the returned n is the
     node count after the batch.
     """
     ops = []
@@ -284,6 +286,10 @@ def random_mixed_batch(rng, n: int, es: EdgeSet, dead: np.ndarray, n_ops: int,
             live.remove(w)
             dead_now.add(w)
             cur_keys = {k for k in cur_keys if (k >> 32) != w and (k & 0xFFFFFFFF) != w}
+        elif p_zero_row > 0 and r < p_add + p_delnode + p_zero_row:
+            w = int(live[rng.integers(len(live))])
+            ops.append((w, 0, OP_ZERO_ROW))
+            cur_keys = {k for k in cur_keys if (k >> 32) != w}
         else:
             u = int(live[rng.integers(len(live))])
             v = int(live[rng.integers(len(live))])

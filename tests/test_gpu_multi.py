@@ -96,7 +96,9 @@ def test_multi_osp_sequence_all_op_kinds(prec):
     nn = n
     batches = []
     for _ in range(6):
-        ops, nn = W.random_mixed_batch(rng, nn, es, dead, 120, protect=tuple(int(s) for s in seeds))
+        # row zeroings (Sec. 3.4.1 read literally) too, seeds included
+        ops, nn = W.random_mixed_batch(rng, nn, es, dead, 120, protect=tuple(int(s) for s in seeds),
+                                       p_zero_row=0.03)
         batches.append(ops)
     eps = 1e-12 if prec == N.OSP_PREC_FP64 else 1e-9
     eng = make_engine(prec, n, src, dst, seeds, 1e-12, max_nodes=n + 4096)

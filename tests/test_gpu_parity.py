@@ -107,24 +107,28 @@ def test_cpi_matches_dense_closed_form():
 
 
 # ---------------------------------------------------------------------------
-def mixed_sequence(rng, n, src, dst, batches, n_ops, seed=0):
+def mixed_sequence(rng, n, src, dst, batches, n_ops, seed=0, p_zero_row=0.0):
     es = W.EdgeSet(src, dst)
     dead = np.zeros(n + batches * n_ops + 8, np.uint8)
     nn = n
     out = []
     for _ in range(batches):
-        ops, nn = W.random_mixed_batch(rng, nn, es, dead, n_ops, protect=(seed,))
+        ops, nn = W.random_mixed_batch(rng, nn, es, dead, n_ops, protect=(seed,),
+                                       p_zero_row=p_zero_row)
         out.append(ops)
     return out
 
 
+@pytest.mark.parametrize("zero_rows", [False, True])
 @pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("prec", PRECS)
-def test_osp_sequence_with_all_op_kinds(prec, order):
-    rng = np.random.default_rng(40 + prec)
+def test_osp_sequence_with_all_op_kinds(prec, order, zero_rows):
+    # zero_rows: batches also hold OSP_OP_ZERO_ROW (the literal node deletion of
+    # Sec. 3.4.1), on the seed too, with edges re-inserted after it
+    rng = np.random.default_rng(40 + prec + 100 * zero_rows)
     n = 400
     src, dst = hub_graph(rng, n=n, m=3000, hub_in=300, hub_out=200, mids=5)
-    batches = mixed_sequence(rng, n, src, dst, 6, 150)
+    batches = mixed_sequence(rng, n, src, dst, 6, 150, p_zero_row=0.04 if zero_rows else 0.0)
     eps = 1e-12
     eng, _ = engine(prec, n, src, dst, eps_init=eps, max_nodes=n + 4096, node_order=order)
     g = O.Graph(n, src, dst)
@@ -135,6 +139,13 @@ def test_osp_sequence_with_all_op_kinds(prec, order):
         assert g.apply(ops, protect=(0,)) == -1
         new = g.csr()
         check_graph(eng, g)
+        # net counts: edges the batch added and removed, from the edge sets
+        old_set = set(zip(np.repeat(np.arange(cur[0].size - 1), np.diff(cur[0])).tolist(),
+                          cur[1].tolist()))
+        new_set = set(zip(np.repeat(np.arange(new[0].size - 1), np.diff(new[0])).tolist(),
+                          new[1].tolist()))
+        assert st["net_inserts"] == len(new_set - old_set)
+        assert st["net_deletes"] == len(old_set - new_set)
         force = st["iterations"] if prec == N.OSP_PREC_FP32_ACC64 else 0
         r_o, q, ost, _ = O.osp(cur, new, r_o, C_RESTART, eps, force_iters=force)
         cur = new

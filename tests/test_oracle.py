@@ -187,6 +187,10 @@ def apply_python(n, edges, dead, ops, protect=()):
                 return p
             edges = {(a, b) for (a, b) in edges if a != u and b != u}
             dead.add(u)
+        elif op == 4:
+            if not (0 <= u < n) or u in dead:
+                return p
+            edges = {(a, b) for (a, b) in edges if a != u}
         else:
             return p
     return n, edges, dead
@@ -198,9 +202,10 @@ def edges_of(g):
     return set(zip(src.tolist(), col.tolist()))
 
 
-@pytest.mark.parametrize("trial", range(8))
+@pytest.mark.parametrize("trial", range(12))
 def test_graph_apply_matches_python_sets(trial):
     rng = np.random.default_rng(500 + trial)
+    p_zero = 0.0 if trial < 8 else 0.06  # the last trials also zero rows
     n = int(rng.integers(5, 40))
     src, dst = random_graph(rng, n, 0.15)
     g = O.Graph(n, src, dst)
@@ -211,7 +216,7 @@ def test_graph_apply_matches_python_sets(trial):
         deadarr = np.zeros(g.n + 64, np.uint8)
         for d in dead:
             deadarr[d] = 1
-        ops, _ = W.random_mixed_batch(rng, g.n, es, deadarr, 25, protect=(0,))
+        ops, _ = W.random_mixed_batch(rng, g.n, es, deadarr, 25, protect=(0,), p_zero_row=p_zero)
         want = apply_python(g.n, edges, dead, ops, protect=(0,))
         bad = g.apply(ops, protect=(0,))
         assert bad == -1 and not isinstance(want, int)
@@ -239,6 +244,8 @@ def test_graph_invalid_batches_leave_graph_unchanged():
         ([(2, 0, 3), (2, 0, 3)], 1),      # double delete
         ([(0, 0, 3)], 0),                 # protected seed
         ([(0, 1, 7)], 0),                 # bad op code
+        ([(2, 0, 3), (2, 0, 4)], 1),      # zero the row of a deleted node
+        ([(0, 0, 4), (9, 0, 4)], 1),      # zero the row of an absent node
     ]
     for rows, bad_at in cases:
         arr = mk(rows)
@@ -252,7 +259,7 @@ def test_graph_invalid_batches_leave_graph_unchanged():
 # ---------------------------------------------------------------------------
 # Offset vector and OSP (Sec. 3.1, Algorithm 1, Theorems 2-4, Sec. 3.3)
 # ---------------------------------------------------------------------------
-def random_case(rng, n=None, n_ops=30, p=0.12, ops_kinds=True):
+def random_case(rng, n=None, n_ops=30, p=0.12, ops_kinds=True, p_zero_row=0.0):
     n = n or int(rng.integers(8, 70))
     src, dst = random_graph(rng, n, p)
     g = O.Graph(n, src, dst)
@@ -261,7 +268,8 @@ def random_case(rng, n=None, n_ops=30, p=0.12, ops_kinds=True):
     es = W.EdgeSet(src, dst)
     dead = np.zeros(n + n_ops + 1, np.uint8)
     if ops_kinds:
-        ops, _ = W.random_mixed_batch(rng, n, es, dead, n_ops, protect=(seed,))
+        ops, _ = W.random_mixed_batch(rng, n, es, dead, n_ops, protect=(seed,),
+                                      p_zero_row=p_zero_row)
     else:
         ops, _ = W.random_mixed_batch(rng, n, es, dead, n_ops, p_add=0, p_delnode=0,
                                       protect=(seed,))
@@ -294,11 +302,12 @@ def test_offset_matches_dense_definition(trial):
     assert np.abs(q).sum() <= 2 * (1 - C_RESTART) * np.abs(ro).sum() + 1e-15
 
 
-@pytest.mark.parametrize("trial", range(8))
+@pytest.mark.parametrize("trial", range(12))
 def test_osp_exactness_theorem2(trial):
-    # Theorem 2: r_old + r_offset equals the RWR vector of the updated graph.
+    # Theorem 2: r_old + r_offset equals the RWR vector of the updated graph
+    # (the last trials also zero rows, the literal node deletion of Sec. 3.4.1).
     rng = np.random.default_rng(1300 + trial)
-    g, old, new, seed, _ = random_case(rng)
+    g, old, new, seed, _ = random_case(rng, p_zero_row=0.0 if trial < 8 else 0.08)
     r_old = O.dense_rwr(old[0].size - 1, *dense_from_csr(*old), seed, C_RESTART)
     r_new, q, st, _ = O.osp(old, new, r_old, C_RESTART, 1e-16)
     want = O.dense_rwr(new[0].size - 1, *dense_from_csr(*new), seed, C_RESTART)
@@ -473,3 +482,43 @@ def O_edges(g):
     rp, col = g.csr()
     src = np.repeat(np.arange(rp.size - 1), np.diff(rp)).astype(np.int32)
     return src, np.asarray(col, np.int32)
+
+
+def test_zero_row_is_the_literal_node_deletion():
+    # Sec. 3.4.1 read literally: deleting node u sets u's row of B~ to zero. The
+    # node keeps its in-edges, so it still collects score but passes none on
+    # (it is a dead-end); with the seed's row zeroed, r = c e_s.
+    n = 5
+    src = [0, 0, 1, 2, 3, 3]
+    dst = [1, 2, 2, 3, 0, 4]
+    g = O.Graph(n, src, dst)
+    ops = np.empty(1, W.UPDATE_DTYPE)
+    ops[0] = (3, 0, W.OP_ZERO_ROW)
+    old = g.csr()
+    assert g.apply(ops, protect=(0,)) == -1
+    assert edges_of(g) == {(0, 1), (0, 2), (1, 2), (2, 3)}
+    new = g.csr()
+    r_old = O.dense_rwr(n, *dense_from_csr(*old), 0, C_RESTART)
+    r_new, _, _, _ = O.osp(old, new, r_old, C_RESTART, 1e-16)
+    # closed form on the zeroed graph: 0 -> {1, 2}, 1 -> 2, 2 -> 3, 3 a dead-end
+    a = 1 - C_RESTART
+    r0 = C_RESTART
+    r1 = a * r0 / 2
+    r2 = a * (r0 / 2 + r1)
+    r3 = a * r2
+    want = np.array([r0, r1, r2, r3, 0.0])
+    assert np.abs(r_new - want).sum() < 1e-14
+    # the seed's own row
+    g2 = O.Graph(n, src, dst)
+    ops[0] = (0, 0, W.OP_ZERO_ROW)
+    assert g2.apply(ops, protect=(0,)) == -1
+    r_seed, _, _, _ = O.osp(old, g2.csr(), r_old, C_RESTART, 1e-16)
+    assert np.abs(r_seed - C_RESTART * np.eye(n)[0]).sum() < 1e-14
+    # edges re-inserted after the zeroing in the same batch are kept
+    g3 = O.Graph(n, src, dst)
+    ops3 = np.empty(3, W.UPDATE_DTYPE)
+    ops3[0] = (3, 4, W.OP_INSERT_EDGE)
+    ops3[1] = (3, 0, W.OP_ZERO_ROW)
+    ops3[2] = (3, 0, W.OP_INSERT_EDGE)
+    assert g3.apply(ops3, protect=(0,)) == -1
+    assert edges_of(g3) == {(0, 1), (0, 2), (1, 2), (2, 3), (3, 0)}
