@@ -20,10 +20,12 @@ using namespace osp;
 namespace {
 
 constexpr int kIngestSmem = kMaxBatch * 8;
-// pinned staging: host ops of a batch first, then the batch size for graph replays
+// pinned staging: host ops of a batch first, then the batch size for graph
+// replays, then the ||x(i)||_1 history read back with the control block
 constexpr size_t kPinnedBytes = 256 * 1024;
 constexpr size_t kPinnedBatchSize = sizeof(osp_update) * kMaxBatch;
-static_assert(kPinnedBatchSize + 64 <= kPinnedBytes, "pinned staging too small");
+constexpr size_t kPinnedHist = kPinnedBatchSize + 64;
+static_assert(kPinnedHist + sizeof(double) * kMaxHist <= kPinnedBytes, "pinned staging too small");
 
 struct HostCtlView {  // the leading fields of Ctl, read back after every call
   Ctl c;
@@ -353,7 +355,9 @@ osp_status reserve_for_batch(osp_ctx* ctx, int64_t U) {
   return OSP_OK;
 }
 
-void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_before) {
+// hist: host copy of the ||x(i)||_1 history (kMaxHist entries)
+void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_before,
+                const double* hist) {
   if (!st) return;
   std::memset(st, 0, sizeof(*st));
   st->iterations = h.iter;
@@ -365,12 +369,8 @@ void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_befor
   st->net_deletes = h.net_ins - (h.m - m_before);
   st->changed_rows = h.n_rec_r;
   st->bad_op = h.status == OSP_EINVAL ? h.bad_op : -1;
-  double hist[2] = {0, 0};
-  cudaMemcpy(&hist[0], ctx->d.l1_hist, sizeof(double), cudaMemcpyDeviceToHost);
-  int k = std::min(h.iter, kMaxHist - 1);
-  cudaMemcpy(&hist[1], ctx->d.l1_hist + k, sizeof(double), cudaMemcpyDeviceToHost);
   st->qoff_l1 = hist[0];
-  st->last_x_l1 = hist[1];
+  st->last_x_l1 = hist[std::max(0, std::min(h.iter, kMaxHist - 1))];
   st->kernel_launches = ctx->launches;
   st->push_frontier = h.push_f;
   st->push_reached = h.push_r;
@@ -383,18 +383,23 @@ void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_befor
 }
 
 osp_status finish_call(osp_ctx* ctx, int64_t m_before, osp_batch_stats* st) {
+  // the history comes back with the control block: one synchronisation per call
+  const double* hist = (const double*)((const char*)ctx->pinned + kPinnedHist);
+  if (st)
+    CK(cudaMemcpyAsync((char*)ctx->pinned + kPinnedHist, ctx->d.l1_hist, sizeof(double) * kMaxHist,
+                       cudaMemcpyDeviceToHost, ctx->stream));
   Ctl h;
   osp_status s = read_ctl(ctx, &h);
   if (s != OSP_OK) return s;
   ctx->last_iters = h.iter;
   if (h.status == OSP_EINVAL) {
-    fill_stats(ctx, h, st, m_before);
+    fill_stats(ctx, h, st, m_before, hist);
     return fail(ctx, OSP_EINVAL, "invalid update batch (first invalid op " +
                                      std::to_string(h.bad_op) + ")");
   }
   if (h.status != 0) {
     ctx->broken = true;
-    fill_stats(ctx, h, st, m_before);
+    fill_stats(ctx, h, st, m_before, hist);
     return fail(ctx, (osp_status)h.status,
                 std::string("device error: ") + osp_status_string((osp_status)h.status));
   }
@@ -402,7 +407,7 @@ osp_status finish_call(osp_ctx* ctx, int64_t m_before, osp_batch_stats* st) {
   ctx->m = h.m;
   ctx->top_r = h.pool_top_r;
   ctx->top_c = h.pool_top_c;
-  fill_stats(ctx, h, st, m_before);
+  fill_stats(ctx, h, st, m_before, hist);
   if (h.noconv) return fail(ctx, OSP_ENOCONV, "iteration cap reached before ||x||_1 <= eps");
   ctx->err.clear();
   return OSP_OK;

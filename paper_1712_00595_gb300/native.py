@@ -219,11 +219,18 @@ class Engine:
                     allow)
         return st.as_dict() if st is not None else None
 
-    def query(self, seed_idx=0, normalize=False):
+    def query(self, seed_idx=0, normalize=False, out=None):
+        """Scores in caller order. out: a float64 host array of at least n
+        entries to write them to (page-locked memory copies fastest); the
+        first n entries are returned."""
         n, _ = self.get_size()
-        out = np.empty(n, np.float64)
+        if out is None:
+            out = np.empty(n, np.float64)
+        elif (not isinstance(out, np.ndarray) or out.dtype != np.float64 or out.ndim != 1
+              or not out.flags.c_contiguous or out.size < n):
+            raise ValueError("out must be a contiguous float64 array of at least %d entries" % n)
         self._check(self._L.osp_query(self._h, int(seed_idx), int(bool(normalize)), _ptr(out)))
-        return out
+        return out[:n]
 
     def query_device(self, out_device, seed_idx=0, normalize=False):
         return self._check(self._L.osp_query_device(self._h, int(seed_idx), int(bool(normalize)),

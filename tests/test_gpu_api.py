@@ -88,3 +88,33 @@ def test_step_times_and_history_are_consistent():
     assert hist[-1] <= 1e-9 < hist[-2]  # the do-while stop
     assert np.all(times > 0)
     eng.close()
+
+
+def test_batch_stats_history_and_query_into_caller_buffer():
+    rng = np.random.default_rng(12)
+    src, dst = W.er_graph(3000, 24000, 9)
+    eng = N.Engine(precision=N.OSP_PREC_FP32_ACC64, device=0, use_graphs=1)
+    eng.load_graph(3000, src, dst)
+    eng.set_seeds([0], 0.15)
+    eng.init_scores(1e-9)
+    es = W.EdgeSet(src, dst)
+    dead = np.zeros(3000 + 64, np.uint8)
+    for _ in range(3):
+        ops, _ = W.random_mixed_batch(rng, 3000, es, dead, 40, p_add=0, p_delnode=0,
+                                      protect=(0,))
+        st = eng.apply_updates(ops, 1e-7)
+        hist = eng.get_l1_history()
+        # ||q_offset||_1 and ||x(k)||_1 of the call come from its step history
+        assert hist.size == st["iterations"] + 1
+        assert st["qoff_l1"] == hist[0] and st["last_x_l1"] == hist[-1]
+        assert st["last_x_l1"] <= 1e-7
+        # the scores written into a caller's (larger) buffer equal a fresh copy
+        buf = np.full(5000, -1.0)
+        got = eng.query(out=buf)
+        assert got.size == 3000 and np.array_equal(got, eng.query())
+        assert np.all(buf[3000:] == -1.0)
+    with pytest.raises(ValueError):
+        eng.query(out=np.zeros(10))
+    with pytest.raises(ValueError):
+        eng.query(out=np.zeros(5000, np.float32))
+    eng.close()
