@@ -84,6 +84,10 @@ def parse():
                    help="serve22: queries read in arrival order, or the newest scores")
     p.add_argument("--log2n", type=int, default=0,
                    help="several-seed workloads: nodes 2^log2n (edges scaled alike; 0 = full size)")
+    p.add_argument("--seed-gather", default="auto", choices=["auto", "regs", "bulk"],
+                   help="seed-block workloads: source rows gathered into registers, or "
+                        "staged in shared memory by bulk asynchronous copies (auto: the "
+                        "engine's choice by row size)")
     p.add_argument("--fp64-seeds", type=int, default=8,
                    help="several-seed workloads: seeds compared with the FP64 replay (0 = skip)")
     return p.parse_args()
@@ -589,8 +593,10 @@ def run_multi(args, rank, world):
     eps_init = 1e-8
     sample = np.linspace(0, S - 1, min(args.fp64_seeds, S)).astype(int) if args.fp64_seeds else []
 
+    gather = {"auto": 0, "regs": N.SEED_GATHER_REGISTERS, "bulk": N.SEED_GATHER_BULK}[args.seed_gather]
+
     def engine(p):
-        e = N.Engine(precision=p, device=local, stream=tstream.cuda_stream)
+        e = N.Engine(precision=p, device=local, stream=tstream.cuda_stream, seed_gather=gather)
         e.load_graph(n, src, dst)
         e.set_seeds(seeds, C_RESTART)
         return e
@@ -631,7 +637,7 @@ def run_multi(args, rank, world):
         "metric": METRIC, "value": value, "unit": "batches/s", "seed_batches_per_s": value * S,
         "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": cfg["precision"], "accumulate": "f64", "data": "synthetic", "config": config,
+        "dtype": cfg["precision"], "accumulate": "f64", "data": "synthetic", "config": dict(config, seed_gather=args.seed_gather),
         "roofline": {"bound": "hbm", "achieved": ab / (prop_ms / 1e3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": ab / (prop_ms / 1e3) / 1e9 / peak, "traffic": None,
                      "kernel": "k_propagate_multi", "peak_kind": peak_kind + " (hbm_gbs copy)",

@@ -112,6 +112,12 @@ typedef struct {
                            (task size 512/1024/2048 x long-list threshold, and node weight
                            2/4/8 with several seeds) on the first CPI steps and keeps the
                            fastest for every later call (osp_get_schedule reports it). */
+    int32_t seed_gather; /* seed block (two or more seeds), how pull steps read source rows:
+                            0 = by row size (2 for rows of at most 256 bytes, i.e. 32 K x the
+                            element size, else 1), 1 = each lane loads its columns of up to eight
+                            rows into registers, 2 = whole rows are copied into a shared-memory
+                            ring by bulk asynchronous copies (cp.async.bulk, mbarrier). Results
+                            are the same up to rounding order. */
 } osp_options;
 
 /* Per-call statistics (the columns of Table 2 plus bookkeeping). */

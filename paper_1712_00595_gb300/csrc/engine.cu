@@ -461,6 +461,17 @@ PropParams prop_params(osp_ctx* ctx, double eps) {
   return pp;
 }
 
+// Seed block of K column groups computed in `precision`: stage source rows by
+// bulk copies? By default only for rows of at most 256 bytes, where it was
+// measured faster (Chung-Lu 2^22, 64 FP32 seeds: 4.16 vs 6.08 ms per pull
+// step); rows of 512 bytes (R-MAT 2^24, 256 bf16 seeds) ran slower (30.7 vs
+// 26.3 ms) and keep register gathers.
+bool seed_bulk(const osp_ctx* ctx, int precision, int K) {
+  if (ctx->opt.seed_gather != 0) return ctx->opt.seed_gather == 2;
+  const int elem = precision == OSP_PREC_FP64 ? 8 : precision == OSP_PREC_FP32_ACC64 ? 4 : 2;
+  return 32 * K * elem <= 256;
+}
+
 // The persistent propagation kernel of one call.
 osp_status enqueue_propagate(osp_ctx* ctx, const PropParams& pp, bool init) {
   if (ctx->S > 1) {
@@ -470,7 +481,7 @@ osp_status enqueue_propagate(osp_ctx* ctx, const PropParams& pp, bool init) {
                                                                        : ctx->opt.precision;
     CK(launch_propagate_multi(ctx->d, pp, prec, prec == ctx->opt.precision ? ctx->grid_multi
                                                                              : ctx->grid_multi_init,
-                              ctx->stream));
+                              seed_bulk(ctx, prec, ctx->d.mu.K), ctx->stream));
   }
   else
     CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
@@ -760,6 +771,10 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
   else osp_default_options(&ctx->opt);
   if (ctx->opt.precision != OSP_PREC_FP64 && ctx->opt.precision != OSP_PREC_FP32_ACC64 &&
       ctx->opt.precision != OSP_PREC_BF16_ACC64) {
+    delete ctx;
+    return OSP_EINVAL;
+  }
+  if (ctx->opt.seed_gather < 0 || ctx->opt.seed_gather > 2) {
     delete ctx;
     return OSP_EINVAL;
   }
@@ -1093,9 +1108,12 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     M.y1 = y1;
     M.hub_acc = hub;
     CK(cudaMemcpyAsync(M.seeds, s_int.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, ctx->stream));
-    ctx->grid_multi = propagate_multi_grid(ctx->opt.precision, K, ctx->num_sms);
-    ctx->grid_multi_init = propagate_multi_grid(
-        ctx->opt.precision == OSP_PREC_FP64 ? OSP_PREC_FP64 : OSP_PREC_FP32_ACC64, K, ctx->num_sms);
+    const int prec_init =
+        ctx->opt.precision == OSP_PREC_FP64 ? OSP_PREC_FP64 : OSP_PREC_FP32_ACC64;
+    ctx->grid_multi = propagate_multi_grid(ctx->opt.precision, K, ctx->num_sms,
+                                           seed_bulk(ctx, ctx->opt.precision, K));
+    ctx->grid_multi_init =
+        propagate_multi_grid(prec_init, K, ctx->num_sms, seed_bulk(ctx, prec_init, K));
     if (ctx->grid_multi <= 0 || ctx->grid_multi_init <= 0) {
       free_multi(ctx);
       return fail(ctx, OSP_ECUDA, "no resident grid for the seed-block kernel");

@@ -56,9 +56,10 @@ __global__ void k_offset_multi_plan(Dev d);
 __global__ void k_multi_cpi_begin(Dev d);
 __global__ void k_gather_col(const double* __restrict__ r, int Sp, int col,
                              const int* __restrict__ ext2int, int n, double* out);
-int propagate_multi_grid(int precision, int K, int num_sms);
+// bulk: the variant that stages source rows in shared memory by bulk copies.
+int propagate_multi_grid(int precision, int K, int num_sms, bool bulk);
 cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int grid,
-                                   cudaStream_t s);
+                                   bool bulk, cudaStream_t s);
 cudaError_t launch_offset_multi(const Dev& d, int grid, cudaStream_t s);
 
 // Host helper: the number of CTAs the persistent kernel can keep resident.

@@ -243,6 +243,203 @@ __device__ __forceinline__ void sum_rows(const int* p, int len, const TY* ys, A 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Whole-row staging through shared memory. Each warp owns two buffers of
+// RingCfg::kRows source rows; a batch of rows of one in-list is copied into a
+// buffer by cp.async.bulk (one copy per row, issued by one lane each), and the
+// buffer's mbarrier completes once the batch's bytes have landed (transaction
+// count = rows x row bytes). The copies need no registers, so many more rows
+// are in flight per warp than with register gathers.
+// ---------------------------------------------------------------------------
+constexpr int kRingBytesPerWarp = 11 * 1024;
+constexpr unsigned long long kRingTimeoutNs = 2000000000ull;  // 2 s
+
+template <typename TY, int K>
+struct RingCfg {
+  static constexpr int kRowBytes = 32 * K * (int)sizeof(TY);  // a multiple of 16
+  static constexpr int kFit = kRingBytesPerWarp / (2 * kRowBytes);
+  static constexpr int kRows = kFit < 1 ? 1 : (kFit > 32 ? 32 : kFit);
+  static constexpr int kBarBytes = 16 * kPropWarps;  // two mbarriers per warp
+  static constexpr int kSmem = kBarBytes + kPropWarps * 2 * kRows * kRowBytes;
+};
+
+struct Ring {
+  unsigned bar;                 // shared address of the warp's mbarrier 0 (mbarrier 1 follows)
+  unsigned rows;                // shared address of the warp's buffer 0 (buffer 1 follows)
+  const unsigned char* rows_g;  // the same, as a generic pointer
+  unsigned phase;               // bit b: parity of buffer b's next completion
+  int buf;                      // the buffer the next batch goes to
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive (the barrier's one expected arrival) and add `bytes` to the
+// transaction count the current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned a, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned a, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Order this thread's generic-proxy accesses to shared memory before later
+// async-proxy ones (a bulk copy overwriting rows that were just read).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_row(unsigned dst, const void* src, unsigned bytes,
+                                              unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Rows u (lane j < cnt holds row j's id) of the gather block into buffer b.
+template <typename TY, int K>
+__device__ __forceinline__ void ring_issue(const Ring& rg, int b, int cnt, int u, const TY* ys) {
+  using C = RingCfg<TY, K>;
+  const int lane = threadIdx.x & 31;
+  const unsigned bar = rg.bar + 8u * (unsigned)b;
+  __syncwarp();  // the warp's reads of buffer b are done ...
+  fence_proxy_async_smem();  // ... and come before the copies that overwrite it
+  if (lane == 0) mbar_arrive_expect(bar, (unsigned)(cnt * C::kRowBytes));
+  __syncwarp();
+  if (lane < cnt)
+    bulk_copy_row(rg.rows + (unsigned)((b * C::kRows + lane) * C::kRowBytes),
+                  ys + (size_t)u * (32 * K), (unsigned)C::kRowBytes, bar);
+}
+
+// Wait for buffer b's batch. Bounded: after 2 s the call's status becomes
+// OSP_ETIMEOUT (the next grid barrier then ends the kernel) and the warp
+// waits once more, again bounded, for its copies in flight.
+__device__ __forceinline__ void ring_wait(Ring& rg, int b, Ctl* ctl) {
+  const unsigned bar = rg.bar + 8u * (unsigned)b;
+  const unsigned par = (rg.phase >> b) & 1u;
+  if (!mbar_try_wait(bar, par)) {
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, par)) {
+      if ((++spins & 255u) == 0 && global_ns() - t0 > kRingTimeoutNs) {
+        if ((threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, (int)OSP_ETIMEOUT);
+        const unsigned long long t1 = global_ns();
+        while (!mbar_try_wait(bar, par) && global_ns() - t1 < kRingTimeoutNs) {
+        }
+        break;
+      }
+    }
+  }
+  rg.phase ^= 1u << b;
+}
+
+// K-element slice of a staged row (plain loads from shared memory).
+template <typename T, int K>
+__device__ __forceinline__ void load_k(const T* p, T (&out)[K]) {
+  constexpr int B = K * (int)sizeof(T);
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i)
+      reinterpret_cast<uint4*>(out)[i] = reinterpret_cast<const uint4*>(p)[i];
+  } else if constexpr (B == 8) {
+    *reinterpret_cast<uint2*>(out) = *reinterpret_cast<const uint2*>(p);
+  } else if constexpr (B == 4) {
+    *reinterpret_cast<unsigned*>(out) = *reinterpret_cast<const unsigned*>(p);
+  } else {
+    *reinterpret_cast<unsigned short*>(out) = *reinterpret_cast<const unsigned short*>(p);
+  }
+}
+
+// acc += the cnt rows staged in buffer b (this lane's K columns).
+template <typename TY, int K, typename A>
+__device__ __forceinline__ void ring_sum(const Ring& rg, int b, int cnt, A (&acc)[K]) {
+  using C = RingCfg<TY, K>;
+  constexpr int Sp = 32 * K;
+  const int lane = threadIdx.x & 31;
+  const TY* row = reinterpret_cast<const TY*>(rg.rows_g + (size_t)b * C::kRows * C::kRowBytes) +
+                  lane * K;
+  int j = 0;
+  if constexpr (K * sizeof(TY) < 64) {  // four rows at a time while they fit in few registers
+    for (; j + 4 <= cnt; j += 4) {
+      alignas(16) TY a[4][K];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) load_k(row + (j + q) * Sp, a[q]);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        acc[k] += (to_acc(a[0][k]) + to_acc(a[1][k])) + (to_acc(a[2][k]) + to_acc(a[3][k]));
+    }
+  } else {
+    for (; j + 2 <= cnt; j += 2) {
+      alignas(16) TY a[2][K];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) load_k(row + (j + q) * Sp, a[q]);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += to_acc(a[0][k]) + to_acc(a[1][k]);
+    }
+  }
+  for (; j < cnt; ++j) {
+    alignas(16) TY a[K];
+    load_k(row + j * Sp, a);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += to_acc(a[k]);
+  }
+}
+
+// acc += the rows of y over in-list entries p[0 .. L), L >= 1, staged in
+// batches of kRows, two batches in flight.
+template <typename TY, int K, typename A>
+__device__ void ring_sum_list(Ring& rg, const Dev& d, const int* p, int L, const TY* ys,
+                              A (&acc)[K]) {
+  constexpr int G = RingCfg<TY, K>::kRows;
+  const int lane = threadIdx.x & 31;
+  auto ids = [&](int s0) -> int {
+    const bool in = lane < min(G, L - s0);
+    int u = in ? __ldg(p + s0 + lane) : 0;
+    if (in && !OSP_GUARD(d.ctl, u >= 0 && u < d.nc, "multi staged piece id", s0, lane, u)) u = 0;
+    return u;
+  };
+  int b = rg.buf;
+  ring_issue<TY, K>(rg, b, min(G, L), ids(0), ys);
+  for (int s0 = 0; s0 < L; s0 += G) {
+    if (s0 + G < L) ring_issue<TY, K>(rg, b ^ 1, min(G, L - s0 - G), ids(s0 + G), ys);
+    ring_wait(rg, b, d.ctl);
+    ring_sum<TY, K, A>(rg, b, min(G, L - s0), acc);
+    b ^= 1;
+  }
+  rg.buf = b;
+}
+
+// A batch of the staged stream: rows s .. s + cnt - 1 of the in-list of the
+// chunk's node lane jc (list at pool_c + off).
+struct RowBatch {
+  int jc, s, cnt;
+  unsigned off;
+  bool first, last;
+};
+
 }  // namespace
 
 // One CTA: offset items of the changed rows (256 entries of old + new list each).
@@ -361,14 +558,33 @@ __global__ void k_gather_col(const double* __restrict__ r, int Sp, int col,
     out[i] = r[(size_t)ext2int[i] * Sp + col];
 }
 
-template <typename TY, int K>
+// kBulk: short and medium in-lists stage whole source rows in shared memory
+// by bulk asynchronous copies (dynamic shared memory RingCfg<TY, K>::kSmem);
+// else each lane gathers its columns of up to eight rows into registers.
+template <typename TY, int K, bool kBulk>
 __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, PropParams pp) {
   using A = typename AccOf<TY>::type;
   constexpr int Sp = 32 * K;
   __shared__ BarShared sh;
   __shared__ double s_part[kPropWarps * Sp];
+  extern __shared__ __align__(128) unsigned char dsm[];
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
+  Ring rg{};
+  if constexpr (kBulk) {
+    using C = RingCfg<TY, K>;
+    const int w = threadIdx.x >> 5;
+    rg.bar = smem_u32(dsm) + 16u * (unsigned)w;
+    const int off = C::kBarBytes + w * 2 * C::kRows * C::kRowBytes;
+    rg.rows = smem_u32(dsm) + (unsigned)off;
+    rg.rows_g = dsm + off;
+    if ((threadIdx.x & 31) == 0) {
+      mbar_init(rg.bar, 1);
+      mbar_init(rg.bar + 8u, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
   const Multi& M = d.mu;
   const int n = ctl->n;
   const long long m = ctl->m;
@@ -456,7 +672,8 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
         A acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = (A)0;
-        sum_rows<TY, K, A>(p, L, ys, acc);
+        if constexpr (kBulk) ring_sum_list<TY, K, A>(rg, d, p, L, ys, acc);
+        else sum_rows<TY, K, A>(p, L, ys, acc);
         A* ha = hub_acc + (size_t)h * Sp + lane * K;
 #pragma unroll
         for (int k = 0; k < K; ++k) atomicAdd(ha + k, acc[k]);
@@ -507,6 +724,81 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
         // and the row of R of the next node load while the current one is summed
         unsigned todo = __ballot_sync(0xffffffffu, lane < cnt && my_len > 0 && my_len <= hub_thr);
         if (!todo) continue;
+        if constexpr (kBulk) {
+          // batches of up to kRows rows of one in-list, nodes in order: the next
+          // batch's copies and the ids of the one after are in flight while a
+          // batch is summed; a node's row of R loads with its first batch
+          constexpr int G = RingCfg<TY, K>::kRows;
+          int pj = 0, plen = 0, ps = 0;
+          unsigned poff = 0;
+          auto next = [&](RowBatch& o) -> bool {
+            if (ps >= plen) {
+              if (!todo) return false;
+              pj = __ffs(todo) - 1;
+              todo &= todo - 1;
+              plen = __shfl_sync(0xffffffffu, my_len, pj);
+              poff = __shfl_sync(0xffffffffu, my_off, pj);
+              ps = 0;
+            }
+            o.jc = pj;
+            o.off = poff;
+            o.s = ps;
+            o.cnt = min(G, plen - ps);
+            o.first = ps == 0;
+            o.last = ps + G >= plen;
+            ps += G;
+            return true;
+          };
+          auto ids_of = [&](const RowBatch& o) -> int {
+            int u = lane < o.cnt ? __ldg(d.pool_c + o.off + (unsigned)(o.s + lane)) : 0;
+            if (lane < o.cnt && !OSP_GUARD(ctl, u >= 0 && u < d.nc, "multi staged id", o.jc, o.s, u))
+              u = 0;
+            return u;
+          };
+          RowBatch c0, c1, c2;
+          next(c0);
+          ring_issue<TY, K>(rg, rg.buf, c0.cnt, ids_of(c0), ys);
+          alignas(16) double rr_n[K];
+          load_cg(M.r + (size_t)(vb + c0.jc) * Sp + lane * K, rr_n);
+          A s_n = scale_of<A>(d, vb + c0.jc);
+          bool h1 = next(c1);
+          int u1 = h1 ? ids_of(c1) : 0;
+          alignas(16) double rr[K];
+          A s = (A)0;
+          A acc[K];
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[k] = (A)0;
+          for (;;) {
+            if (c0.first) {
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                rr[k] = rr_n[k];
+                acc[k] = (A)0;
+              }
+              s = s_n;
+            }
+            const int b = rg.buf;
+            if (h1) {
+              ring_issue<TY, K>(rg, b ^ 1, c1.cnt, u1, ys);
+              if (c1.first) {
+                load_cg(M.r + (size_t)(vb + c1.jc) * Sp + lane * K, rr_n);
+                s_n = scale_of<A>(d, vb + c1.jc);
+              }
+            }
+            const bool h2 = h1 && next(c2);
+            const int u2 = h2 ? ids_of(c2) : 0;
+            ring_wait(rg, b, ctl);
+            ring_sum<TY, K, A>(rg, b, c0.cnt, acc);
+            if (c0.last) finish_row<TY, K, A>(d, vb + c0.jc, acc, s, rr, act, yd, l1);
+            if (!h1) break;
+            rg.buf = b ^ 1;
+            c0 = c1;
+            c1 = c2;
+            h1 = h2;
+            u1 = u2;
+          }
+          continue;
+        }
         int jn = __ffs(todo) - 1;
         todo &= todo - 1;
         int len_n = __shfl_sync(0xffffffffu, my_len, jn);
@@ -550,28 +842,42 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
 
 namespace {
 
+struct MultiFn {
+  const void* fn;
+  int smem;  // dynamic shared memory bytes
+};
+
+template <typename TY, int K>
+MultiFn multi_fn_k(bool bulk) {
+  if (bulk) return {(const void*)k_propagate_multi<TY, K, true>, RingCfg<TY, K>::kSmem};
+  return {(const void*)k_propagate_multi<TY, K, false>, 0};
+}
+
 template <typename TY>
-const void* multi_fn(int K) {
+MultiFn multi_fn(int K, bool bulk) {
   switch (K) {
-    case 1: return (const void*)k_propagate_multi<TY, 1>;
-    case 2: return (const void*)k_propagate_multi<TY, 2>;
-    case 4: return (const void*)k_propagate_multi<TY, 4>;
-    default: return (const void*)k_propagate_multi<TY, 8>;
+    case 1: return multi_fn_k<TY, 1>(bulk);
+    case 2: return multi_fn_k<TY, 2>(bulk);
+    case 4: return multi_fn_k<TY, 4>(bulk);
+    default: return multi_fn_k<TY, 8>(bulk);
   }
 }
 
-const void* pick_multi(int precision, int K) {
-  if (precision == OSP_PREC_FP64) return multi_fn<double>(K);
-  if (precision == OSP_PREC_FP32_ACC64) return multi_fn<float>(K);
-  return multi_fn<__nv_bfloat16>(K);
+MultiFn pick_multi(int precision, int K, bool bulk) {
+  if (precision == OSP_PREC_FP64) return multi_fn<double>(K, bulk);
+  if (precision == OSP_PREC_FP32_ACC64) return multi_fn<float>(K, bulk);
+  return multi_fn<__nv_bfloat16>(K, bulk);
 }
 
 }  // namespace
 
-int propagate_multi_grid(int precision, int K, int num_sms) {
+int propagate_multi_grid(int precision, int K, int num_sms, bool bulk) {
+  const MultiFn f = pick_multi(precision, K, bulk);
+  if (f.smem > 0 &&
+      cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem) != cudaSuccess)
+    return 0;
   int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pick_multi(precision, K), kPropThreads, 0) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, f.fn, kPropThreads, f.smem) != cudaSuccess ||
       bps <= 0)
     return 0;
   bps = bps > 4 ? 4 : bps;
@@ -580,12 +886,12 @@ int propagate_multi_grid(int precision, int K, int num_sms) {
 }
 
 cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int grid,
-                                   cudaStream_t s) {
+                                   bool bulk, cudaStream_t s) {
   Dev dd = d;
   PropParams p = pp;
   void* args[] = {&dd, &p};
-  return cudaLaunchCooperativeKernel(pick_multi(precision, d.mu.K), dim3(grid), dim3(kPropThreads),
-                                     args, 0, s);
+  const MultiFn f = pick_multi(precision, d.mu.K, bulk);
+  return cudaLaunchCooperativeKernel(f.fn, dim3(grid), dim3(kPropThreads), args, (size_t)f.smem, s);
 }
 
 cudaError_t launch_offset_multi(const Dev& d, int grid, cudaStream_t s) {

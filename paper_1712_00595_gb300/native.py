@@ -20,6 +20,7 @@ LIB_PATH = os.environ.get("OSP_LIBRARY") or os.path.join(HERE, "_build", "libosp
 OSP_OK, OSP_EINVAL, OSP_ENOMEM, OSP_ECUDA, OSP_ETIMEOUT, OSP_ENOCONV, OSP_ESTATE, OSP_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6, -7)
 OSP_PREC_FP64, OSP_PREC_FP32_ACC64, OSP_PREC_BF16_ACC64 = 0, 1, 2
+SEED_GATHER_REGISTERS, SEED_GATHER_BULK = 1, 2  # osp_options.seed_gather
 UPDATE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("op", "<i4")])
 
 TOPK_NOALLOC_MAX_N = 16777216  # OSP_TOPK_NOALLOC_MAX_N
@@ -40,7 +41,7 @@ class osp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("max_nodes", C.c_int64), ("push_alpha", C.c_double), ("push_beta", C.c_double),
                 ("max_iter", C.c_int32), ("node_order", C.c_int32), ("use_graphs", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("seed_gather", C.c_int32)]
 
 
 class osp_batch_stats(C.Structure):
@@ -150,7 +151,7 @@ class Engine:
 
     def __init__(self, precision=OSP_PREC_FP32_ACC64, device=0, stream=None, max_nodes=0,
                  push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0, use_graphs=False,
-                 autotune=False):
+                 autotune=False, seed_gather=0):
         L = load_library()
         opt = osp_options()
         L.osp_default_options(C.byref(opt))
@@ -164,6 +165,7 @@ class Engine:
         opt.node_order = node_order
         opt.use_graphs = int(bool(use_graphs))
         opt.autotune = int(bool(autotune))
+        opt.seed_gather = int(seed_gather)
         h = C.c_void_p()
         s = L.osp_create(C.byref(h), C.byref(opt))
         if s != OSP_OK:

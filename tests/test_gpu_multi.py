@@ -62,15 +62,19 @@ def check_graph(eng, g):
     assert np.array_equal(ptr, cp) and np.array_equal(idx, row)
 
 
+GATHERS = [N.SEED_GATHER_REGISTERS, N.SEED_GATHER_BULK]
+
+
+@pytest.mark.parametrize("gather", GATHERS)
 @pytest.mark.parametrize("S", [5, 40, 100, 256])
 @pytest.mark.parametrize("prec", [N.OSP_PREC_FP64, N.OSP_PREC_FP32_ACC64])
-def test_multi_cpi_lockstep(prec, S):
+def test_multi_cpi_lockstep(prec, S, gather):
     rng = np.random.default_rng(100 + S)
     n = 1200
     src, dst = hub_graph(rng, n, 9000, 1100, 500, 6)
     seeds = rng.permutation(n)[:S].astype(np.int32)
     eps = 1e-10
-    eng = make_engine(prec, n, src, dst, seeds, eps)
+    eng = make_engine(prec, n, src, dst, seeds, eps, seed_gather=gather)
     iters, q, last = eng.get_seed_stats()
     assert iters.size == S and np.all(iters >= 1)
     assert np.allclose(q, C_RESTART, rtol=1e-12)  # ||x(0)||_1 = c for CPI
@@ -84,8 +88,9 @@ def test_multi_cpi_lockstep(prec, S):
     eng.close()
 
 
+@pytest.mark.parametrize("gather", GATHERS)
 @pytest.mark.parametrize("prec", [N.OSP_PREC_FP64, N.OSP_PREC_FP32_ACC64, N.OSP_PREC_BF16_ACC64])
-def test_multi_osp_sequence_all_op_kinds(prec):
+def test_multi_osp_sequence_all_op_kinds(prec, gather):
     rng = np.random.default_rng(7 + prec)
     n = 1200
     src, dst = hub_graph(rng, n, 8000, 1100, 300, 5)
@@ -101,7 +106,7 @@ def test_multi_osp_sequence_all_op_kinds(prec):
                                        p_zero_row=0.03)
         batches.append(ops)
     eps = 1e-12 if prec == N.OSP_PREC_FP64 else 1e-9
-    eng = make_engine(prec, n, src, dst, seeds, 1e-12, max_nodes=n + 4096)
+    eng = make_engine(prec, n, src, dst, seeds, 1e-12, max_nodes=n + 4096, seed_gather=gather)
     g = O.Graph(n, src, dst)
     cur = g.csr()
     it0, _, _ = eng.get_seed_stats()
