@@ -426,9 +426,11 @@ def run_ours(args, rank, world):
     r_mixed = eng.query()
     schedule = eng.get_schedule()
     # the paper's baseline on the GPU: CPI from scratch on the final graph at the same eps
-    st_cpi = eng.init_scores(args.eps)
-    cpi_gpu = {"ms": st_cpi["ms_update"] + st_cpi["ms_propagate"],
-               "iterations": int(st_cpi["iterations"])}
+    cpi_gpu = None
+    if not args.no_extras:
+        st_cpi = eng.init_scores(args.eps)
+        cpi_gpu = {"ms": st_cpi["ms_update"] + st_cpi["ms_propagate"],
+                   "iterations": int(st_cpi["iterations"])}
     t_local = sum(ms) / 1e3
     t_max = dist_max(t_local, world)
     value = world * K / t_max
