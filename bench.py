@@ -598,7 +598,8 @@ def run_multi(args, rank, world):
     gather = {"auto": 0, "regs": N.SEED_GATHER_REGISTERS, "bulk": N.SEED_GATHER_BULK}[args.seed_gather]
 
     def engine(p):
-        e = N.Engine(precision=p, device=local, stream=tstream.cuda_stream, seed_gather=gather)
+        e = N.Engine(precision=p, device=local, stream=tstream.cuda_stream, seed_gather=gather,
+                     autotune=args.autotune)
         e.load_graph(n, src, dst)
         e.set_seeds(seeds, C_RESTART)
         return e
@@ -627,6 +628,7 @@ def run_multi(args, rank, world):
     ms = [a.elapsed_time(b) for a, b in ev]
     steps_us = eng.get_step_times()
     r_s = {int(j): eng.query(int(j)) for j in sample}
+    schedule = list(eng.get_schedule())
     eng.close()
     t = dist_max(sum(ms) / 1e3, world)
     value = world * K / t
@@ -639,7 +641,8 @@ def run_multi(args, rank, world):
         "metric": METRIC, "value": value, "unit": "batches/s", "seed_batches_per_s": value * S,
         "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": cfg["precision"], "accumulate": "f64", "data": "synthetic", "config": dict(config, seed_gather=args.seed_gather),
+        "dtype": cfg["precision"], "accumulate": "f64", "data": "synthetic", "config": dict(config, seed_gather=args.seed_gather, autotune=bool(args.autotune),
+                       schedule=schedule),
         "roofline": {"bound": "hbm", "achieved": ab / (prop_ms / 1e3) / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": ab / (prop_ms / 1e3) / 1e9 / peak, "traffic": None,
                      "kernel": "k_propagate_multi", "peak_kind": peak_kind + " (hbm_gbs copy)",
