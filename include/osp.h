@@ -321,6 +321,19 @@ const char *osp_last_error(const osp_ctx *ctx);
 /* Static name of a status code. */
 const char *osp_status_string(osp_status s);
 
+/* Failure-detection self-test on `device` (no context needed). Every wait of
+ * the engine's persistent kernels is bounded (2 s of device time); this runs
+ * one of those waits on scratch memory of its own:
+ *   which 0: the grid barrier, 4 CTAs;
+ *   which 1: the mbarrier of a staged-row batch (two 128-byte rows announced).
+ * lose = 0: every CTA arrives / both rows land; returns OSP_OK.
+ * lose = 1: one CTA never arrives / the second row is never copied; the wait
+ * runs out, the kernel returns and OSP_ETIMEOUT is returned (about 2 s for
+ * the barrier, 4 s for the mbarrier, which waits once more for its copies).
+ * The device stays usable. OSP_EINVAL for a bad which; OSP_ECUDA on a CUDA
+ * error. */
+osp_status osp_selftest_wait(int32_t device, int32_t which, int32_t lose);
+
 #ifdef __cplusplus
 }
 #endif

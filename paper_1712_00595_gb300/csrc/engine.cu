@@ -763,6 +763,35 @@ const char* osp_last_error(const osp_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int64_t osp_max_batch(void) { return kMaxBatch; }
 
+osp_status osp_selftest_wait(int32_t device, int32_t which, int32_t lose) {
+  if (which != 0 && which != 1) return OSP_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return OSP_ECUDA;
+  Ctl* ctl = nullptr;
+  float* src = nullptr;
+  cudaStream_t st = nullptr;
+  osp_status r = OSP_ECUDA;
+  std::vector<float> h(64);
+  for (int i = 0; i < 64; ++i) h[i] = 1.0f + (float)i;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaMalloc(&ctl, sizeof(Ctl)) == cudaSuccess &&
+      cudaMalloc(&src, sizeof(float) * 64) == cudaSuccess &&
+      cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
+      cudaMemcpyAsync(src, h.data(), sizeof(float) * 64, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+      launch_selftest(ctl, src, which, lose ? 1 : 0, st) == cudaSuccess &&
+      cudaStreamSynchronize(st) == cudaSuccess) {
+    Ctl c;
+    if (cudaMemcpy(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      if (c.status != 0) r = (osp_status)c.status;
+      else r = c.iter == 1 ? OSP_OK : OSP_ECUDA;  // completed, and (staging) the rows intact
+    }
+  }
+  cudaGetLastError();
+  if (src) cudaFree(src);
+  if (ctl) cudaFree(ctl);
+  if (st) cudaStreamDestroy(st);
+  return r;
+}
+
 osp_status osp_create(osp_ctx** out, const osp_options* opt) {
   if (!out) return OSP_EINVAL;
   *out = nullptr;

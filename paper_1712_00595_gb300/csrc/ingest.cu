@@ -212,7 +212,7 @@ __global__ void k_cpi_begin(Dev d) {
 __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_update* __restrict__ ops,
                                                            int U) {
   extern __shared__ unsigned long long skey[];
-  __shared__ int s_bad, s_ndel, s_nclr;
+  __shared__ int s_bad, s_ndel, s_nclr, s_anyclr;
   __shared__ long long s_reins;
   __shared__ unsigned s_flags[kIngestThreads];
   Ctl* ctl = d.ctl;
@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
     s_bad = kNoPos;
     s_ndel = 0;
     s_nclr = 0;
+    s_anyclr = 0;
     s_reins = 0;
   }
   __syncthreads();
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       else atomicMin(&s_bad, p);
     } else if (o.op == OSP_OP_ZERO_ROW) {
       // the last zeroing of a row in the batch voids the row's earlier edge ops
+      s_anyclr = 1;
       if (o.u >= 0 && o.u < n_old + run) atomicMax(&d.clr_pos[o.u], p);
       else atomicMin(&s_bad, p);
     }
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
     osp_update o = load_op(ops, p, d);
     unsigned long long key = kNoKey;
     if ((o.op == OSP_OP_INSERT_EDGE || o.op == OSP_OP_DELETE_EDGE) && d.del_pos[o.u] == kNoPos &&
-        d.del_pos[o.v] == kNoPos && d.clr_pos[o.u] < p)
+        d.del_pos[o.v] == kNoPos && (!s_anyclr || d.clr_pos[o.u] < p))
       key = ((unsigned long long)o.u << 39) | ((unsigned long long)o.v << 14) | (unsigned)p;
     skey[p] = key;
   }
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
       present_before = lr <= lc ? contains_i(d.pool_r + d.off_r[u], lr, v)
                                 : contains_i(d.pool_c + d.off_c[v], lc, u);
     }
-    if (d.clr_pos[u] >= 0) {
+    if (s_anyclr && d.clr_pos[u] >= 0) {
       // u's row was zeroed before this op: the merge drops every old entry of
       // the row (and u from the old in-lists), so a surviving edge is written
       // again as an insertion, but it is not a new edge
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_ingest(Dev d, const osp_upda
   // ---- node deletions and additions ----
   for (int p = lo; p < hi; ++p) {
     if (ops[p].op == OSP_OP_DELETE_NODE) d.del_nodes[atomicAdd(&s_ndel, 1)] = load_op(ops, p, d).u;
-    if (ops[p].op == OSP_OP_ZERO_ROW) {
+    if (s_anyclr && ops[p].op == OSP_OP_ZERO_ROW) {
       const int u = load_op(ops, p, d).u;
       if (d.clr_pos[u] == p) d.clr_nodes[atomicAdd(&s_nclr, 1)] = u;  // once per row
     }

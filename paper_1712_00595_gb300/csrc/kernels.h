@@ -61,6 +61,9 @@ int propagate_multi_grid(int precision, int K, int num_sms, bool bulk);
 cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int grid,
                                    bool bulk, cudaStream_t s);
 cudaError_t launch_offset_multi(const Dev& d, int grid, cudaStream_t s);
+// Failure-detection self-test: which 0 = grid barrier, 1 = staged-row mbarrier;
+// lose != 0 makes the wait run out (src: 64 floats on the device).
+cudaError_t launch_selftest(Ctl* ctl, const float* src, int which, int lose, cudaStream_t s);
 
 // Host helper: the number of CTAs the persistent kernel can keep resident.
 int propagate_grid(int fp32, int num_sms);

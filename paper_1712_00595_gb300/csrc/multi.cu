@@ -894,6 +894,55 @@ cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int preci
   return cudaLaunchCooperativeKernel(f.fn, dim3(grid), dim3(kPropThreads), args, (size_t)f.smem, s);
 }
 
+// ---------------------------------------------------------------------------
+// Failure-detection self-tests: the bounded waits of the persistent kernels
+// are made to run out on purpose (a CTA that never arrives; an mbarrier whose
+// announced bytes never all land), and the status word must report it.
+// ---------------------------------------------------------------------------
+__global__ void k_selftest_barrier(Ctl* ctl, int lose) {
+  __shared__ BarShared sh;
+  if (lose && blockIdx.x == 0) return;  // this CTA never arrives
+  if (bar_arrive(ctl, sh) && threadIdx.x == 0) ctl->iter = 1;
+  bar_release(ctl, sh);
+}
+
+__global__ void k_selftest_stage(Ctl* ctl, const float* src, int lose) {
+  using C = RingCfg<float, 1>;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  Ring rg{};
+  rg.bar = smem_u32(dsm);
+  rg.rows = smem_u32(dsm) + C::kBarBytes;
+  rg.rows_g = dsm + C::kBarBytes;
+  if (threadIdx.x == 0) {
+    mbar_init(rg.bar, 1);
+    mbar_init(rg.bar + 8u, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // two rows announced; with `lose` only the first is copied
+    mbar_arrive_expect(rg.bar, 2u * C::kRowBytes);
+    bulk_copy_row(rg.rows, src, C::kRowBytes, rg.bar);
+    if (!lose) bulk_copy_row(rg.rows + C::kRowBytes, src + 32, C::kRowBytes, rg.bar);
+  }
+  __syncwarp();
+  ring_wait(rg, 0, ctl);
+  if (threadIdx.x == 0 && *(volatile int*)&ctl->status == 0) {
+    const float* r = reinterpret_cast<const float*>(rg.rows_g);
+    ctl->iter = (r[0] == src[0] && r[63] == src[63]) ? 1 : 2;  // both rows arrived intact
+  }
+}
+
+cudaError_t launch_selftest(Ctl* ctl, const float* src, int which, int lose, cudaStream_t s) {
+  if (which == 0) {
+    k_selftest_barrier<<<4, 64, 0, s>>>(ctl, lose);
+  } else {
+    k_selftest_stage<<<1, 32, RingCfg<float, 1>::kBarBytes + 2 * RingCfg<float, 1>::kRowBytes, s>>>(
+        ctl, src, lose);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_offset_multi(const Dev& d, int grid, cudaStream_t s) {
   switch (d.mu.K) {
     case 1: k_offset_multi<1><<<grid, 256, 0, s>>>(d); break;

@@ -33,7 +33,7 @@ EXPORTED = [
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
     "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
     "osp_set_seed_iterations", "osp_get_schedule", "osp_query_slots", "osp_topk_async",
-    "osp_topk_wait",
+    "osp_topk_wait", "osp_selftest_wait",
 ]
 
 
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
             "osp_query_slots": (C.c_int, [P, i32]),
             "osp_topk_async": (C.c_int, [P, i32, i32, i32, C.c_int]),
             "osp_topk_wait": (C.c_int, [P, i32, P, P, P]),
+            "osp_selftest_wait": (C.c_int, [i32, i32, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -129,6 +130,13 @@ def _ptr(a) -> C.c_void_p:
     if isinstance(a, int):
         return C.c_void_p(a)
     return a.ctypes.data_as(C.c_void_p)
+
+
+def selftest_wait(which, lose, device=0):
+    """osp_selftest_wait: run one bounded wait of the persistent kernels
+    (which 0 = grid barrier, 1 = staged-row mbarrier), made to run out when
+    lose is true. Returns the status code (OSP_OK or OSP_ETIMEOUT)."""
+    return load_library().osp_selftest_wait(int(device), int(which), int(bool(lose)))
 
 
 def topk_noalloc(scores_device, n, k, ids_device, out_scores_device, k_out_device,

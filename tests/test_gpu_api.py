@@ -118,3 +118,25 @@ def test_batch_stats_history_and_query_into_caller_buffer():
     with pytest.raises(ValueError):
         eng.query(out=np.zeros(5000, np.float32))
     eng.close()
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_waits_run_out_and_report_timeout(which):
+    # failure detection without a GPU fault: a CTA that never reaches the grid
+    # barrier (which 0) or a staged-row batch whose second row never lands
+    # (which 1) ends in OSP_ETIMEOUT within the wait's limit, and the device
+    # keeps working
+    import time
+    assert N.selftest_wait(which, False) == N.OSP_OK
+    t0 = time.perf_counter()
+    assert N.selftest_wait(which, True) == N.OSP_ETIMEOUT
+    dt = time.perf_counter() - t0
+    assert 1.0 < dt < 20.0
+    src, dst = W.er_graph(500, 4000, 3)
+    eng = N.Engine(precision=N.OSP_PREC_FP64, device=0)
+    eng.load_graph(500, src, dst)
+    eng.set_seeds([0, 1, 2], 0.15)
+    eng.init_scores(1e-10)
+    r = eng.query(0)
+    assert np.all(np.isfinite(r)) and 0.5 < r.sum() <= 1 + 1e-9 and r[0] >= 0.15
+    eng.close()
