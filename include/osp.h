@@ -130,7 +130,9 @@ typedef struct {
     int64_t n_nodes;         /* node ids in use after the call (dead ones included) */
     int64_t m_edges;         /* live directed edges after the call */
     int64_t net_inserts;     /* edges the batch actually added */
-    int64_t net_deletes;     /* edges the batch actually removed (node deletions included) */
+    int64_t net_deletes;     /* edges the batch actually removed (node deletions and row
+                                zeroings included); a batch above osp_max_batch() sums
+                                both counts over its sub-batches */
     int64_t changed_rows;    /* rows u with B~[u] != A~[u] (candidates) */
     int64_t bad_op;          /* OSP_EINVAL from a batch: index of the first invalid op; else -1 */
     int64_t push_frontier;   /* sum over push steps of the frontier size |F(i-1)| */

@@ -208,7 +208,7 @@ def test_graph_replay_matches_eager_launches(seeds):
     nn = n
     batches = []
     for k in (5, 150, 300, 17, 150, 1):
-        ops, nn = W.random_mixed_batch(rng, nn, es, dead, k, protect=tuple(seeds))
+        ops, nn = W.random_mixed_batch(rng, nn, es, dead, k, protect=tuple(seeds), p_zero_row=0.03)
         batches.append(ops)
     engs = []
     for graphs in (False, True):
@@ -587,4 +587,41 @@ def test_topk_matches_ranking_of_the_score_vector(order):
     ids, sc = eng.topk(20)
     want_ids, want_sc = O.topk(eng.query(), 20)
     assert ids.size == 7 and np.array_equal(ids, want_ids) and np.array_equal(sc, want_sc)
+    eng.close()
+
+
+def test_zero_rows_across_sub_batches():
+    """Row zeroings (OSP_OP_ZERO_ROW) at and around the sub-batch boundaries of
+    a large batch, with edge ops on the same rows before and after them: the
+    graph and the scores equal the oracle's (exact mode)."""
+    rng = np.random.default_rng(73)
+    n = 3000
+    src, dst = hub_graph(rng, n=n, m=60000, hub_in=2500, hub_out=900, mids=12)
+    gen = np.random.default_rng(6)
+    sampler = lambda k: (gen.integers(0, n, k), gen.integers(0, n, k))  # noqa: E731
+    big = W.sized_update_stream(src, dst, n, [40000], 3, sampler)[0].copy()
+    for p in (100, 16383, 16384, 20000, 32767, 32768, 39998):
+        u = int(big["u"][p + 1]) if p + 1 < big.size else int(big["u"][p - 1])
+        big[p] = (u, 0, W.OP_ZERO_ROW)
+    big[16390] = (int(src[0]), 0, W.OP_ZERO_ROW)
+    big[16391] = (int(src[0]), int(dst[0]), W.OP_INSERT_EDGE)  # re-inserted after the zeroing
+    eng, _ = engine(N.OSP_PREC_FP64, n, src, dst, eps_init=1e-13)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    r_o, _, _ = O.cpi(*cur, 0, C_RESTART, 1e-13)
+    m0 = g.m
+    st = eng.apply_updates(big, 1e-13)
+    assert g.apply(big, protect=(0,)) == -1
+    new = g.csr()
+    check_graph(eng, g)
+    old_set = set(zip(np.repeat(np.arange(n), np.diff(cur[0])).tolist(), cur[1].tolist()))
+    new_set = set(zip(np.repeat(np.arange(n), np.diff(new[0])).tolist(), new[1].tolist()))
+    # counted per sub-batch: an edge added by one sub-batch and removed by a
+    # later one counts in both columns
+    assert st["net_inserts"] - st["net_deletes"] == g.m - m0 and st["m_edges"] == g.m
+    assert st["net_inserts"] >= len(new_set - old_set)
+    assert st["net_deletes"] >= len(old_set - new_set)
+    r_o, q, _, _ = O.osp(cur, new, r_o, C_RESTART, 1e-13)
+    assert st["qoff_l1"] == pytest.approx(np.abs(q).sum(), rel=1e-9, abs=1e-15)
+    assert l1(eng.query(), r_o) <= 1e-10
     eng.close()
