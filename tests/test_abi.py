@@ -64,3 +64,17 @@ def test_host_only_entry_points(lib):
     lib.osp_default_options(C.byref(opt))
     assert opt.precision == N.OSP_PREC_FP32_ACC64 and opt.device == 0
     assert lib.osp_create(None, None) == N.OSP_EINVAL
+
+
+def test_host_side_argument_checks(lib):
+    # rejected before any CUDA call, so they run without a GPU
+    assert lib.osp_selftest_wait(0, 7, 0) == N.OSP_EINVAL
+    opt = N.osp_options()
+    lib.osp_default_options(C.byref(opt))
+    assert opt.seed_gather == 0
+    opt.seed_gather = 5
+    h = C.c_void_p()
+    assert lib.osp_create(C.byref(h), C.byref(opt)) == N.OSP_EINVAL
+    opt.seed_gather = 0
+    opt.precision = 9
+    assert lib.osp_create(C.byref(h), C.byref(opt)) == N.OSP_EINVAL
