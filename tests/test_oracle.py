@@ -522,3 +522,38 @@ def test_zero_row_is_the_literal_node_deletion():
     ops3[2] = (3, 0, W.OP_INSERT_EDGE)
     assert g3.apply(ops3, protect=(0,)) == -1
     assert edges_of(g3) == {(0, 1), (0, 2), (1, 2), (2, 3), (3, 0)}
+
+
+def test_seed_block_input_generators():
+    # Chung-Lu: distinct unordered pairs, exact count, heavy-tailed degrees
+    # that follow the weights (the top-weight nodes carry the largest degrees)
+    g, lo, hi = W.chung_lu_graph(4096, 4096 * 8, seed=11)
+    assert lo.size == 4096 * 8 and np.all(lo < hi)
+    assert np.unique(W.edge_keys(lo, hi)).size == lo.size
+    deg = np.bincount(np.concatenate([lo, hi]), minlength=4096)
+    assert deg.mean() == 16.0
+    top = g.perm[:8]  # the largest weights, capped at sqrt(sum w) = 256
+    assert deg[top].min() > 8 * deg.mean() and deg.max() < 2 * 256
+    # undirected stream: both directions of every pair, insertions absent,
+    # deletions present, sizes as asked
+    sizes = W.log_uniform_sizes(6, 10, 1000, seed=4)
+    assert np.all((sizes >= 10) & (sizes < 1000))
+    stream = W.undirected_update_stream(lo, hi, 4096, sizes, 5, g.sample)
+    es = W.EdgeSet(np.concatenate([lo, hi]), np.concatenate([hi, lo]))
+    for k, ops in zip(sizes, stream):
+        assert ops.size == 2 * k
+        fwd = set(zip(ops["u"].tolist(), ops["v"].tolist(), ops["op"].tolist()))
+        assert all((v, u, op) in fwd for (u, v, op) in fwd)
+        ins = ops[ops["op"] == W.OP_INSERT_EDGE]
+        dels = ops[ops["op"] == W.OP_DELETE_EDGE]
+        assert not es.contains(W.edge_keys(ins["u"], ins["v"])).any()
+        assert es.contains(W.edge_keys(dels["u"], dels["v"])).all()
+        es.apply(W.edge_keys(ins["u"], ins["v"]), W.edge_keys(dels["u"], dels["v"]))
+    # node operations: valid in sequence, seeds never deleted
+    _, s, d = W.rmat_graph(10, 6000, seed=2)
+    batches = W.node_op_stream(s, d, 1024, 3, 20, 8, 10, 40, seed=6, protect=(0, 5))
+    gr = O.Graph(1024, s, d)
+    for ops in batches:
+        assert gr.apply(ops, protect=(0, 5)) == -1
+        assert (ops["op"] == W.OP_ADD_NODE).sum() == 20
+        assert (ops["op"] == W.OP_DELETE_NODE).sum() == 10
