@@ -261,6 +261,9 @@ struct RingCfg {
   static constexpr int kRows = kFit < 1 ? 1 : (kFit > 32 ? 32 : kFit);
   static constexpr int kBarBytes = 16 * kPropWarps;  // two mbarriers per warp
   static constexpr int kSmem = kBarBytes + kPropWarps * 2 * kRows * kRowBytes;
+  // bulk copies need 16-byte aligned addresses and sizes
+  static_assert(kRowBytes % 16 == 0 && kBarBytes % 16 == 0, "staged rows must stay 16-byte aligned");
+  static_assert(kSmem <= 100 * 1024, "two CTAs per SM must fit with the static shared memory");
 };
 
 struct Ring {
