@@ -557,3 +557,39 @@ def test_seed_block_input_generators():
         assert gr.apply(ops, protect=(0, 5)) == -1
         assert (ops["op"] == W.OP_ADD_NODE).sum() == 20
         assert (ops["op"] == W.OP_DELETE_NODE).sum() == 10
+
+
+@pytest.mark.parametrize("trial", range(3))
+def test_batch_equals_its_ops_applied_one_at_a_time(trial):
+    # Several ops on one row in one batch (reading c12): Delta A is the rows
+    # after the whole batch minus the rows before it, so in exact mode one OSP
+    # call over the batch equals one OSP call per op, and both equal the dense
+    # solve on the final graph (Theorem 2).
+    rng = np.random.default_rng(2100 + trial)
+    n = 40
+    src, dst = random_graph(rng, n, 0.1)
+    es = W.EdgeSet(src, dst)
+    dead = np.zeros(n + 64, np.uint8)
+    ops, _ = W.random_mixed_batch(rng, n, es, dead, 30, protect=(0,), p_zero_row=0.05)
+    # a row touched several times: insert, delete, re-insert the same edge
+    extra = np.empty(3, W.UPDATE_DTYPE)
+    extra[0] = (1, 2, W.OP_INSERT_EDGE)
+    extra[1] = (1, 2, W.OP_DELETE_EDGE)
+    extra[2] = (1, 3, W.OP_INSERT_EDGE)
+    ops = np.concatenate([extra, ops])
+    g_all, g_one = O.Graph(n, src, dst), O.Graph(n, src, dst)
+    start = g_all.csr()
+    r0 = O.dense_rwr(n, src, dst, 0, C_RESTART)
+    assert g_all.apply(ops, protect=(0,)) == -1
+    r_all, _, _, _ = O.osp(start, g_all.csr(), r0, C_RESTART, 1e-16)
+    r_one, cur = r0, start
+    for k in range(ops.size):
+        assert g_one.apply(ops[k:k + 1], protect=(0,)) == -1
+        new = g_one.csr()
+        r_one, _, _, _ = O.osp(cur, new, r_one, C_RESTART, 1e-16)
+        cur = new
+    assert edges_of(g_all) == edges_of(g_one)
+    n_new = cur[0].size - 1
+    want = O.dense_rwr(n_new, *dense_from_csr(*cur), 0, C_RESTART)
+    assert np.abs(r_all - want).sum() < 1e-12
+    assert np.abs(r_one - want).sum() < 1e-11
