@@ -593,3 +593,32 @@ def test_batch_equals_its_ops_applied_one_at_a_time(trial):
     want = O.dense_rwr(n_new, *dense_from_csr(*cur), 0, C_RESTART)
     assert np.abs(r_all - want).sum() < 1e-12
     assert np.abs(r_one - want).sum() < 1e-11
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+def test_error_accumulates_at_most_linearly_over_batches(eps):
+    # Reading c5: each batch leaves an untaken tail whose residual is the last
+    # step's x(k+1), of norm <= (1-c) eps, and the residuals add up; so after B
+    # batches from a CPI start at eps_init, ||r - r*||_1 <= ||rho||_1 / c with
+    # ||rho||_1 <= (1-c) eps_init + B (1-c) eps. Checked against the dense
+    # solve and the residual computed directly.
+    rng = np.random.default_rng(int(-math.log10(eps)) * 31)
+    n = 60
+    src, dst = random_graph(rng, n, 0.08)
+    g = O.Graph(n, src, dst)
+    es = W.EdgeSet(src, dst)
+    dead = np.zeros(n + 400, np.uint8)
+    cur = g.csr()
+    eps_init = 1e-4
+    r, _, _ = O.cpi(*cur, 0, C_RESTART, eps_init)
+    B = 12
+    for b in range(B):
+        ops, _ = W.random_mixed_batch(rng, g.n, es, dead, 15, protect=(0,))
+        assert g.apply(ops, protect=(0,)) == -1
+        new = g.csr()
+        r, _, _, _ = O.osp(cur, new, r, C_RESTART, eps)
+        cur = new
+        rho = O.residual_l1(*cur, 0, C_RESTART, r)
+        assert rho <= (1 - C_RESTART) * (eps_init + (b + 1) * eps) + 1e-13
+        want = O.dense_rwr(cur[0].size - 1, *dense_from_csr(*cur), 0, C_RESTART)
+        assert np.abs(r - want).sum() <= rho / C_RESTART + 1e-12
