@@ -203,28 +203,34 @@ class Clocks:
             with open(keep, "w") as f:
                 f.write(open(self.path).read())
         os.unlink(self.path)
-        if len(rows) < 2:
-            return None
-        hdr = [h.strip() for h in rows[0]]
-        sm, smax, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows[1:]:
-            if len(r) != len(hdr):
-                continue
-            d = dict(zip(hdr, [x.strip() for x in r]))
-            try:
-                sm.append(float(d["clocks.current.sm [MHz]"].split()[0]))
-                smax = max(smax, float(d["clocks.max.sm [MHz]"].split()[0]))
-            except Exception:
-                continue
-            for nm in names:
-                key = [k for k in d if k.startswith("clocks_event_reasons." + nm)]
-                if key and d[key[0]].lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clock_samples(rows)
+
+
+def parse_clock_samples(rows):
+    """nvidia-smi CSV rows (header first) -> median SM clock, max clock and the
+    throttle reasons seen active during the samples (None without samples)."""
+    if len(rows) < 2:
+        return None
+    hdr = [h.strip() for h in rows[0]]
+    sm, smax, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows[1:]:
+        if len(r) != len(hdr):
+            continue
+        d = dict(zip(hdr, [x.strip() for x in r]))
+        try:
+            sm.append(float(d["clocks.current.sm [MHz]"].split()[0]))
+            smax = max(smax, float(d["clocks.max.sm [MHz]"].split()[0]))
+        except Exception:
+            continue
+        for nm in names:
+            key = [k for k in d if k.startswith("clocks_event_reasons." + nm)]
+            if key and d[key[0]].lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def dist_setup(args):

@@ -73,3 +73,27 @@ def test_rank_accuracy_matches_scipy_spearman():
     top_a = set(np.argsort(-a, kind="stable")[:100].tolist())
     assert bench.rank_accuracy(a, a) == {"spearman": 1.0, "top100_overlap": 1.0}
     assert 0.0 <= got["top100_overlap"] <= 1.0 and len(top_a) == 100
+
+
+def test_clock_samples_parsing():
+    hdr = ["index", " clocks.current.sm [MHz]", " clocks.max.sm [MHz]", " power.draw [W]",
+           " clocks_event_reasons.active", " clocks_event_reasons.hw_slowdown",
+           " clocks_event_reasons.hw_thermal_slowdown", " clocks_event_reasons.sw_thermal_slowdown",
+           " clocks_event_reasons.sw_power_cap"]
+    row = lambda mhz, cap: ["0", f" {mhz} MHz", " 2070 MHz", " 900.00 W", " 0x0", " Not Active",  # noqa: E731
+                            " Not Active", " Not Active", " Active" if cap else " Not Active"]
+    out = bench.parse_clock_samples([hdr, row(2070, False), row(1980, True), row(2070, False),
+                                     ["0", "garbled"]])
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+    assert bench.parse_clock_samples([hdr]) is None
+
+
+def test_traffic_record_is_ignored_when_the_kernel_changed(monkeypatch):
+    # the committed DRAM bytes belong to the kernel sources they were taken on
+    cur = bench.kernel_source_hash()
+    rec = bench.traffic_from_profile()
+    if rec is not None:
+        assert rec > 1e8
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16 if cur != "0" * 16 else "1")
+    assert bench.traffic_from_profile() is None
