@@ -17,6 +17,11 @@ input.
 """
 from __future__ import annotations
 
+import ctypes as C
+import os
+import subprocess
+import threading
+
 import numpy as np
 
 # One update operation, laid out exactly as ``osp_update`` in include/osp.h.
@@ -61,6 +66,97 @@ def _fill_unique(draw, m: int, chunk: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Native sampler (gen.c): counter-based draws, sort and de-duplication of
+# edge keys, multi-threaded; it draws inputs only.
+# --------------------------------------------------------------------------
+_GEN_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gen.c")
+_GEN_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libgen.so")
+_gen_lock = threading.Lock()
+_gen_lib = None
+
+
+def build_gen(force: bool = False) -> str:
+    """Compile gen.c with gcc into the package's _build folder."""
+    os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
+    if force or not os.path.exists(_GEN_LIB) or os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", tmp,
+                               _GEN_SRC])
+        os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _gen():
+    global _gen_lib
+    with _gen_lock:
+        if _gen_lib is None:
+            L = C.CDLL(build_gen())
+            P, i64, i32, u64, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_double
+            L.gen_rmat.argtypes = [u64, i32, dbl, dbl, dbl, i64, i64, P, P, i32, i32]
+            L.gen_chunglu.argtypes = [u64, P, i64, i64, i64, P, P, i32, i32]
+            L.keys_sort_unique.restype = i64
+            L.keys_sort_unique.argtypes = [P, i64, i32, i32]
+            L.keys_merge_unique.restype = i64
+            L.keys_merge_unique.argtypes = [P, i64, P, i64, P]
+            L.keys_apply.restype = i64
+            L.keys_apply.argtypes = [P, i64, P, i64, P, i64, P]
+            _gen_lib = L
+    return _gen_lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+THREADS = 0  # native sampler threads (0: one per core, at most 32); results do not depend on it
+
+
+def _nthreads() -> int:
+    return THREADS if THREADS > 0 else max(1, min(32, os.cpu_count() or 1))
+
+
+def _key_bits(n: int) -> int:
+    return 32 + max(1, int(n - 1).bit_length())
+
+
+def sort_unique_keys(keys: np.ndarray, n: int) -> np.ndarray:
+    """Distinct keys of ``keys`` ascending (rejected draws dropped); ids below n."""
+    keys = np.ascontiguousarray(keys, np.uint64).copy()
+    k = _gen().keys_sort_unique(_ptr(keys), keys.size, _key_bits(n), _nthreads())
+    if k < 0:
+        raise MemoryError("key sort")
+    return keys[:k]
+
+
+def _unique_draws(draw, m: int, n: int) -> np.ndarray:
+    """The first ``m`` distinct keys of a counter-based sampler, ascending.
+
+    draw(start, count) returns draws start .. start + count - 1 as keys
+    (rejections as all-ones keys). Rounds draw the missing count (plus a
+    margin) until m distinct keys exist; a surplus from the last round is
+    thinned at evenly spaced positions of the sorted set."""
+    have = np.empty(0, np.uint64)
+    start, k = 0, m + m // 16 + 1024
+    while True:
+        cand = sort_unique_keys(draw(start, k), n)
+        start += k
+        if have.size == 0:
+            have = cand
+        else:
+            out = np.empty(have.size + cand.size, np.uint64)
+            got = _gen().keys_merge_unique(_ptr(have), have.size, _ptr(cand), cand.size, _ptr(out))
+            have = out[:got]
+        if have.size >= m:
+            break
+        k = 2 * (m - have.size) + 1024
+    extra = have.size - m
+    if extra > 0:
+        pos = ((np.arange(extra, dtype=np.float64) + 0.5) * (have.size / extra)).astype(np.int64)
+        have = np.delete(have, pos)
+    return have
+
+
+# --------------------------------------------------------------------------
 # Graphs
 # --------------------------------------------------------------------------
 def er_graph(n: int, m: int, seed: int):
@@ -83,6 +179,8 @@ class RMat:
     Vertex ids are relabelled by a seeded random permutation so that hubs are
     not clustered at small ids; the same permutation is used for the edges of
     the initial graph and for later insertions drawn from the same sampler.
+    Draws come from the counter-based native sampler (gen.c): the graph's
+    candidates and the stream samples use two streams keyed from ``seed``.
     """
 
     def __init__(self, scale: int, a=0.57, b=0.19, c=0.19, d=0.05, seed: int = BASE_SEED,
@@ -92,32 +190,27 @@ class RMat:
         self.p = (a, b, c, d)
         self.rng = rng_for(seed)
         self.perm = self.rng.permutation(self.n).astype(np.int64) if permute else None
+        self.key_graph, self.key_sample = (int(x) for x in self.rng.integers(0, 1 << 63, 2))
+        self.drawn = 0
+
+    def _draw(self, key, start, k, keep_loops):
+        a, b, c, _ = self.p
+        out = np.empty(k, np.uint64)
+        _gen().gen_rmat(key, self.scale, a, b, c, start, k, _ptr(self.perm), _ptr(out),
+                        int(keep_loops), _nthreads())
+        return out
 
     def sample(self, k: int):
-        a, b, c, _ = self.p
-        u = np.zeros(k, np.int64)
-        v = np.zeros(k, np.int64)
-        for _lvl in range(self.scale):
-            r = self.rng.random(k)
-            ubit = r >= (a + b)
-            vbit = ((r >= a) & (r < a + b)) | (r >= a + b + c)
-            u = (u << 1) | ubit
-            v = (v << 1) | vbit
-        if self.perm is not None:
-            u = self.perm[u]
-            v = self.perm[v]
-        return u, v
+        """The next k draws of the sample stream as (u, v), self-loops included."""
+        keys = self._draw(self.key_sample, self.drawn, int(k), True)
+        self.drawn += int(k)
+        return ((keys >> np.uint64(32)).astype(np.int64),
+                (keys & np.uint64(0xFFFFFFFF)).astype(np.int64))
 
     def graph(self, m: int):
-        def draw(k):
-            out = []
-            for s in range(0, k, 1 << 24):
-                u, v = self.sample(min(1 << 24, k - s))
-                ok = u != v
-                out.append(edge_keys(u[ok], v[ok]))
-            return np.concatenate(out)
-
-        return split_keys(_fill_unique(draw, m, 1 << 24))
+        """m distinct directed edges without self-loops, sorted by (u, v)."""
+        keys = _unique_draws(lambda s, k: self._draw(self.key_graph, s, k, False), m, self.n)
+        return split_keys(keys)
 
 
 class ChungLu:
@@ -127,7 +220,7 @@ class ChungLu:
     (i + 1) ** (-1 / (beta - 1)), scaled so that the weights sum to
     mean_degree * n and capped at sqrt(sum w); an edge's endpoints are drawn
     independently with probability proportional to w. Ids are relabelled by a
-    seeded permutation, as for R-MAT.
+    seeded permutation, as for R-MAT; draws come from the native sampler.
     """
 
     def __init__(self, n: int, mean_degree: float = 16.0, beta: float = 2.1,
@@ -140,27 +233,28 @@ class ChungLu:
         self.cdf = np.cumsum(w)
         self.cdf /= self.cdf[-1]
         self.perm = self.rng.permutation(n).astype(np.int64)
+        self.key_graph, self.key_sample = (int(x) for x in self.rng.integers(0, 1 << 63, 2))
+        self.drawn = 0
+
+    def _draw(self, key, start, k, keep_loops):
+        out = np.empty(k, np.uint64)
+        _gen().gen_chunglu(key, _ptr(self.cdf), self.n, start, k, _ptr(self.perm), _ptr(out),
+                           int(keep_loops), _nthreads())
+        return out
 
     def sample(self, k: int):
-        u = np.searchsorted(self.cdf, self.rng.random(k), side="right")
-        v = np.searchsorted(self.cdf, self.rng.random(k), side="right")
-        u = np.minimum(u, self.n - 1)
-        v = np.minimum(v, self.n - 1)
-        return self.perm[u], self.perm[v]
+        """The next k draws of the sample stream as (u, v), self-loops included."""
+        keys = self._draw(self.key_sample, self.drawn, int(k), True)
+        self.drawn += int(k)
+        return ((keys >> np.uint64(32)).astype(np.int64),
+                (keys & np.uint64(0xFFFFFFFF)).astype(np.int64))
 
     def graph(self, m_undirected: int):
         """m_undirected distinct unordered pairs {u, v}, u != v, returned as
         (lo, hi) arrays (the caller stores both directions)."""
-        def draw(k):
-            out = []
-            for s in range(0, k, 1 << 24):
-                u, v = self.sample(min(1 << 24, k - s))
-                ok = u != v
-                lo, hi = np.minimum(u[ok], v[ok]), np.maximum(u[ok], v[ok])
-                out.append(edge_keys(lo, hi))
-            return np.concatenate(out)
-
-        return split_keys(_fill_unique(draw, m_undirected, 1 << 24))
+        keys = _unique_draws(lambda s, k: self._draw(self.key_graph, s, k, False), m_undirected,
+                             self.n)
+        return split_keys(keys)
 
 
 def chung_lu_graph(n: int, m_undirected: int, seed: int = BASE_SEED, **kw):
@@ -189,24 +283,91 @@ def max_out_degree_seed(n: int, src: np.ndarray) -> int:
 # Update streams
 # --------------------------------------------------------------------------
 class EdgeSet:
-    """Sorted array of directed edge keys, used to draw valid updates."""
+    """A set of directed edge keys, used to draw valid updates.
+
+    ``keys`` is the sorted array; batches applied with ``apply`` are kept as
+    small pending insert / delete sets and merged into the array (one linear
+    pass) only when ``keys`` is read or the pending sets grow large."""
+
+    _PENDING_MAX = 1 << 20
 
     def __init__(self, src, dst):
-        self.keys = np.sort(edge_keys(np.asarray(src), np.asarray(dst)))
+        keys = edge_keys(np.asarray(src), np.asarray(dst))
+        if keys.size > 1 and not bool(np.all(keys[1:] > keys[:-1])):
+            # distinct keys, ascending (the native radix sort over the bits in use)
+            bits = max(1, int(keys.max()).bit_length())
+            keys = np.ascontiguousarray(keys)
+            k = _gen().keys_sort_unique(_ptr(keys), keys.size, bits, _nthreads())
+            keys = keys[:k]
+        self._base = keys
+        self._ins = np.empty(0, np.uint64)  # present, not in _base
+        self._del = np.empty(0, np.uint64)  # in _base, not present
+
+    @property
+    def keys(self) -> np.ndarray:
+        if self._ins.size or self._del.size:
+            out = np.empty(self._base.size + self._ins.size, np.uint64)
+            k = _gen().keys_apply(_ptr(self._base), self._base.size, _ptr(self._ins), self._ins.size,
+                                  _ptr(self._del), self._del.size, _ptr(out))
+            self._base = out[:k]
+            self._ins = np.empty(0, np.uint64)
+            self._del = np.empty(0, np.uint64)
+        return self._base
+
+    @keys.setter
+    def keys(self, value):
+        self._base = np.asarray(value, np.uint64)
+        self._ins = np.empty(0, np.uint64)
+        self._del = np.empty(0, np.uint64)
+
+    @property
+    def size(self) -> int:
+        return int(self._base.size + self._ins.size - self._del.size)
+
+    def _in_base(self, keys):
+        if self._base.size == 0:
+            return np.zeros(np.shape(keys), bool)
+        pos = np.minimum(np.searchsorted(self._base, keys), self._base.size - 1)
+        return self._base[pos] == keys
 
     def contains(self, keys: np.ndarray) -> np.ndarray:
-        pos = np.searchsorted(self.keys, keys)
-        pos = np.minimum(pos, self.keys.size - 1)
-        return self.keys[pos] == keys
+        keys = np.asarray(keys, np.uint64)
+        got = self._in_base(keys)
+        if self._del.size:
+            got &= ~np.isin(keys, self._del)
+        if self._ins.size:
+            got |= np.isin(keys, self._ins)
+        return got
 
     def apply(self, ins_keys: np.ndarray, del_keys: np.ndarray):
-        if del_keys.size:
-            pos = np.searchsorted(self.keys, np.sort(del_keys))
-            self.keys = np.delete(self.keys, pos)
-        if ins_keys.size:
-            ins = np.sort(ins_keys)
-            pos = np.searchsorted(self.keys, ins)
-            self.keys = np.insert(self.keys, pos, ins)
+        """Remove del_keys (present), then add ins_keys (absent)."""
+        ins = np.unique(np.asarray(ins_keys, np.uint64))
+        dels = np.unique(np.asarray(del_keys, np.uint64))
+        if dels.size:
+            self._ins = np.setdiff1d(self._ins, dels, assume_unique=True)
+            self._del = np.union1d(self._del, dels[self._in_base(dels)])
+        if ins.size:
+            base = self._in_base(ins)
+            self._del = np.setdiff1d(self._del, ins[base], assume_unique=True)
+            self._ins = np.union1d(self._ins, ins[~base])
+        if self._ins.size + self._del.size > self._PENDING_MAX:
+            _ = self.keys
+
+    def draw_present(self, rng, count: int) -> np.ndarray:
+        """``count`` keys drawn uniformly (with replacement) from the present keys."""
+        nb, ni = self._base.size, self._ins.size
+        out = np.empty(0, np.uint64)
+        while out.size < count:
+            i = rng.integers(0, nb + ni, 2 * (count - out.size) + 8)
+            cand = np.where(i < nb, self._base[np.minimum(i, max(nb - 1, 0))],
+                            self._ins[np.maximum(i - nb, 0)] if ni else np.uint64(0))
+            ok = i >= nb
+            if self._del.size:
+                ok |= ~np.isin(cand, self._del)
+            else:
+                ok |= True
+            out = np.concatenate([out, cand[ok]])
+        return out[:count]
 
 
 def _pack(ins_keys, del_keys, rng) -> np.ndarray:
@@ -381,7 +542,7 @@ def node_op_stream(src, dst, n: int, batches: int, n_new: int, new_degree: int, 
         ins = _draw_absent(es, k_ins, live_pairs, rng)
         dels = np.empty(0, np.uint64)
         while dels.size < k_del:
-            cand = es.keys[rng.integers(0, es.keys.size, 2 * (k_del - dels.size) + 16)]
+            cand = es.draw_present(rng, 2 * (k_del - dels.size) + 16)
             cu, cv = split_keys(cand)
             cand = cand[~dead[cu] & ~dead[cv]]
             dels = _first_unique(np.concatenate([dels, cand]))
