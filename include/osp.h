@@ -48,7 +48,9 @@ typedef enum {
     OSP_ENOTSUP = -7   /* valid request this build does not implement */
 } osp_status;
 
-/* Arithmetic of the propagation (Sec. 2.2 / Algorithm 1 loop).
+/* Arithmetic of the propagation (Sec. 2.2 / Algorithm 1 loop). Running sums and
+ * stored scores are always FP64: an FP32 sum with Kahan compensation costs the
+ * same 8 bytes per entry and is less exact, so it is not offered.
  * FP64:        gather vector, products and every sum in double.
  * FP32_ACC64:  gather vector and products in float (in-row sums of the pull
  *              step in float); scores r, the offset vector, push-step
@@ -56,8 +58,11 @@ typedef enum {
  * BF16_ACC64:  batches store the gather vector as bfloat16 (rounded to
  *              nearest), products and in-row sums in float, r / offset /
  *              stopping test in double; osp_init_scores runs as FP32_ACC64.
- *              Two or more seeds only (osp_set_seeds returns OSP_ENOTSUP for
- *              one). */
+ *              Each stored value's rounding residual is carried into the
+ *              rounding of the same entry at the next step (error feedback),
+ *              so the stored values' rounding errors telescope instead of
+ *              adding up over the steps. Two or more seeds only
+ *              (osp_set_seeds returns OSP_ENOTSUP for one). */
 typedef enum {
     OSP_PREC_FP64 = 0,
     OSP_PREC_FP32_ACC64 = 1,
@@ -118,6 +123,21 @@ typedef struct {
                             rows into registers, 2 = whole rows are copied into a shared-memory
                             ring by bulk asynchronous copies (cp.async.bulk, mbarrier). Results
                             are the same up to rounding order. */
+    int32_t seed_group;  /* seed block: columns per column group of the pull steps (32, 64, 128
+                            or 256, at most Sp; 0 = 32 for bf16 gather rows, else Sp, one
+                            group). A pull step walks the graph
+                            once per group that still has a running column, so groups whose
+                            seeds have all stopped cost nothing; inside a group, a lane whose
+                            columns have all stopped loads and stores nothing. */
+    int32_t deterministic; /* != 0: every propagation step pulls (no push steps) and long
+                              in-lists combine their pieces in a fixed order, so one input
+                              gives the same bits on every run (the one-seed path). */
+    int64_t l2_hot_bytes; /* seed block with node_order 1: bytes of L2 given to the gather rows
+                             of the highest out-degree nodes (kept in L2 before other lines);
+                             0 = 60% of the device's L2, < 0 = none. */
+    int64_t hbm_budget_bytes; /* device memory the context may allocate (graph store, score
+                                 blocks, query slots together); a call that would exceed it
+                                 returns OSP_ENOMEM and allocates nothing more. 0 = no limit. */
 } osp_options;
 
 /* Per-call statistics (the columns of Table 2 plus bookkeeping). */
@@ -143,6 +163,12 @@ typedef struct {
     int32_t reserved;
     int64_t pull_dst_nodes;  /* nodes with a nonempty in-list (destinations of a pull step) */
     int64_t pull_src_nodes;  /* nodes with a nonempty out-list (sources a pull step gathers) */
+    double residual_bound;   /* bound on ||rho||_1, rho = c q - (I - (1-c) B~^T) r, of the scores
+                                stored after the call (exact arithmetic; the max over seeds when
+                                S > 1). Each call adds its untaken tail's residual x(k+1),
+                                ||x(k+1)||_1 <= (1-c) ||x(k)||_1 (Algorithm 1 stopping rule,
+                                Theorem 4); osp_init_scores restarts it. Then
+                                ||r - r*||_1 <= residual_bound / c. */
 } osp_batch_stats;
 
 /* Fill *opt with defaults (FP32_ACC64, device 0, engine-owned stream). */
@@ -285,6 +311,17 @@ osp_status osp_export_graph(osp_ctx *ctx, int direction, int64_t *ptr, int32_t *
 
 /* Current node count (ids in use, dead ones included) and live edge count. */
 osp_status osp_get_size(osp_ctx *ctx, int64_t *n, int64_t *m);
+
+/* Current node count (ids in use, dead ones included); -1 for a NULL context. */
+int64_t osp_num_nodes(const osp_ctx *ctx);
+
+/* Per seed, the residual bound of osp_batch_stats.residual_bound (host array of up to
+ * cap entries, count in *count = min(S, cap)): ||rho_j||_1 of seed j's stored scores
+ * is at most out[j] in exact arithmetic, so ||r_j - r_j*||_1 <= out[j] / c. */
+osp_status osp_get_residual_bounds(osp_ctx *ctx, double *out, int32_t cap, int32_t *count);
+
+/* Device memory the context holds now (bytes of its own allocations). */
+int64_t osp_device_bytes(const osp_ctx *ctx);
 
 /* Per seed of the last init/apply call (host arrays of up to cap entries, any of
  * them NULL to skip): the steps the seed ran, ||x(0)||_1 (its ||q_offset||_1)

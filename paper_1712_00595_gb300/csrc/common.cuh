@@ -69,27 +69,38 @@ struct Ctl {
   long long push_f, push_r;    // sums of |F(i-1)| and |F(i)| over push steps
   int seed;
   int multi;                   // 1: several seeds (the Multi block of Dev), 0: one seed
+  int n_grp;                   // several seeds: column groups with a running column ...
+  int grp[8];                  // ... and their indices, for the next pull step
   double c;
 };
 
 constexpr int kMaxSeeds = 256;
 
 // Several seeds tracked together: column j of each n x Sp block belongs to
-// seed j (Sp = 32 K, K in {1, 2, 4, 8}; columns S .. Sp-1 stay zero). Lane l of
-// a warp owns the K contiguous columns [K l, K l + K) of a row.
+// the seed placed in column j (Sp = 32 K, K in {1, 2, 4, 8}; columns S .. Sp-1
+// stay zero). R and the offset accumulator are [node][Sp]. The propagation
+// kernel works on column groups of G = 32 KG columns (KG divides K; lane l
+// owns columns [KG l, KG l + KG) of a group) and lays its gather blocks out
+// group-major, [group][node][G].
 struct Multi {
   int S, Sp, K;
-  int* seeds;          // [S] internal ids
+  int KG;              // columns per lane in a column group of the batch kernel
+  int KG_init;         // ... of the initial CPI (float rows when batches use bf16)
+  int* seeds;          // [S] internal ids, by column
   double* r;           // [nc Sp] scores (unnormalised r_temp)
   double* xacc;        // [nc Sp] offset accumulator
-  void* y0; void* y1;  // [nc Sp] gather vectors (double, float or bf16)
+  void* y0; void* y1;  // [nc Sp] gather blocks (double, float or bf16), group-major
+  void* e;             // [nc Sp] bf16 rounding residuals of the gather block (bf16 only)
   double* part;        // [kMaxGrid Sp] per-CTA |x| partials
   int* active;         // [Sp] 1 while the column still propagates
+  int* touched;        // [Sp] 1: the column has a nonzero offset entry in this call
   int* col_iters;      // [Sp] steps run per column
   double* col_q;       // [Sp] ||x(0)||_1 per column
   double* col_last;    // [Sp] ||x(k)||_1 at the column's stop
+  double* res_bound;   // [Sp] bound on ||rho||_1 of the stored column (see osp_get_residual_bounds)
   int* force;          // [Sp] > 0: the column runs exactly that many steps
   void* hub_acc;       // [hubs Sp] (float or double) partial sums of long in-lists
+  int* hub_cnt;        // [hubs 8] pieces done per long in-list and column group
 };
 
 // Every device pointer of one engine, passed to kernels by value.
@@ -163,6 +174,7 @@ struct PropParams {
   double alpha;
   double beta;
   int fp32;
+  int hot_n;  // seed block: gather rows of internal ids below hot_n are kept in L2 first
 };
 
 // ---------------------------------------------------------------------------

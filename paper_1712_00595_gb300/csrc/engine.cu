@@ -25,7 +25,8 @@ constexpr int kIngestSmem = kMaxBatch * 8;
 constexpr size_t kPinnedBytes = 256 * 1024;
 constexpr size_t kPinnedBatchSize = sizeof(osp_update) * kMaxBatch;
 constexpr size_t kPinnedHist = kPinnedBatchSize + 64;
-static_assert(kPinnedHist + sizeof(double) * kMaxHist <= kPinnedBytes, "pinned staging too small");
+constexpr size_t kPinnedRes = kPinnedHist + sizeof(double) * kMaxHist;  // per-seed residual bounds
+static_assert(kPinnedRes + sizeof(double) * kMaxSeeds <= kPinnedBytes, "pinned staging too small");
 
 struct HostCtlView {  // the leading fields of Ctl, read back after every call
   Ctl c;
@@ -99,6 +100,10 @@ struct osp_ctx {
   int fixed_iters = 0;
   int grid_prop = 0;
   int last_iters = 0;
+  std::vector<int32_t> col_of;  // several seeds: seed j -> its column of the seed block
+  double res_bound = 0.0;       // one seed: bound on ||rho||_1 of the stored scores
+  int64_t hbm_used = 0;         // bytes of device memory held by the context
+  std::map<void*, size_t> dsizes;
 
   Dev d{};
   std::vector<void*> allocs;
@@ -147,16 +152,31 @@ osp_status dalloc(osp_ctx* ctx, T** p, size_t count, int fill = 0,
                   std::vector<void*>* list = nullptr) {
   void* q = nullptr;
   size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (ctx->opt.hbm_budget_bytes > 0 && ctx->hbm_used + (int64_t)bytes > ctx->opt.hbm_budget_bytes)
+    return fail(ctx, OSP_ENOMEM, "HBM budget of " + std::to_string(ctx->opt.hbm_budget_bytes) +
+                                     " bytes would be exceeded (" + std::to_string(ctx->hbm_used) +
+                                     " held, " + std::to_string(bytes) + " asked)");
   cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, OSP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
+  ctx->hbm_used += (int64_t)bytes;
+  ctx->dsizes[q] = bytes;
   e = cudaMemsetAsync(q, fill, bytes, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
   (list ? list : &ctx->allocs)->push_back(q);
   *p = (T*)q;
   return OSP_OK;
+}
+
+void dfree(osp_ctx* ctx, void* p) {
+  auto it = ctx->dsizes.find(p);
+  if (it != ctx->dsizes.end()) {
+    ctx->hbm_used -= (int64_t)it->second;
+    ctx->dsizes.erase(it);
+  }
+  cudaFree(p);
 }
 
 void drop_graphs(osp_ctx* ctx) {
@@ -172,24 +192,25 @@ void free_slots(osp_ctx* ctx) {
   for (auto& q : ctx->qslots)
     if (q.done) cudaEventDestroy(q.done);
   ctx->qslots.clear();
-  for (void* p : ctx->qallocs) cudaFree(p);
+  for (void* p : ctx->qallocs) dfree(ctx, p);
   ctx->qallocs.clear();
 }
 
 void free_multi(osp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graphs(ctx);
-  for (void* p : ctx->mallocs) cudaFree(p);
+  for (void* p : ctx->mallocs) dfree(ctx, p);
   ctx->mallocs.clear();
   ctx->d.mu = Multi{};
   ctx->S = 1;
   ctx->seed_force_max = 0;
+  ctx->col_of.clear();
 }
 
 void free_all(osp_ctx* ctx) {
   free_slots(ctx);
   free_multi(ctx);
-  for (void* p : ctx->allocs) cudaFree(p);
+  for (void* p : ctx->allocs) dfree(ctx, p);
   ctx->allocs.clear();
   ctx->d = Dev{};
   ctx->ops_stage = nullptr;
@@ -376,6 +397,12 @@ void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_befor
   st->push_reached = h.push_r;
   st->pull_dst_nodes = h.n_dst_nz;
   st->pull_src_nodes = h.n_src_nz;
+  if (ctx->S > 1) {
+    const double* rb = (const double*)((const char*)ctx->pinned + kPinnedRes);
+    for (int j = 0; j < ctx->S; ++j) st->residual_bound = std::max(st->residual_bound, rb[j]);
+  } else {
+    st->residual_bound = ctx->res_bound;
+  }
   float a = 0.f, b = 0.f;
   if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st->ms_update = a;
   if (cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess) st->ms_propagate = b;
@@ -383,15 +410,20 @@ void fill_stats(osp_ctx* ctx, const Ctl& h, osp_batch_stats* st, int64_t m_befor
 }
 
 osp_status finish_call(osp_ctx* ctx, int64_t m_before, osp_batch_stats* st) {
-  // the history comes back with the control block: one synchronisation per call
+  // the history (and the seed block's residual bounds) come back with the
+  // control block: one synchronisation per call
   const double* hist = (const double*)((const char*)ctx->pinned + kPinnedHist);
-  if (st)
-    CK(cudaMemcpyAsync((char*)ctx->pinned + kPinnedHist, ctx->d.l1_hist, sizeof(double) * kMaxHist,
-                       cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync((char*)ctx->pinned + kPinnedHist, ctx->d.l1_hist, sizeof(double) * kMaxHist,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->S > 1 && st)
+    CK(cudaMemcpyAsync((char*)ctx->pinned + kPinnedRes, ctx->d.mu.res_bound,
+                       sizeof(double) * ctx->S, cudaMemcpyDeviceToHost, ctx->stream));
   Ctl h;
   osp_status s = read_ctl(ctx, &h);
   if (s != OSP_OK) return s;
   ctx->last_iters = h.iter;
+  if (ctx->S == 1 && h.status == 0)  // the untaken tail: ||x(k+1)||_1 <= (1-c) ||x(k)||_1
+    ctx->res_bound += (1.0 - ctx->c) * hist[std::max(0, std::min(h.iter, kMaxHist - 1))];
   if (h.status == OSP_EINVAL) {
     fill_stats(ctx, h, st, m_before, hist);
     return fail(ctx, OSP_EINVAL, "invalid update batch (first invalid op " +
@@ -458,7 +490,25 @@ PropParams prop_params(osp_ctx* ctx, double eps) {
   pp.alpha = ctx->opt.push_alpha > 0 ? ctx->opt.push_alpha : kPushAlpha;
   pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : kPushBeta;
   pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
+  pp.hot_n = 0;
   return pp;
+}
+
+// Seed block: gather rows of internal ids below hot_n get L2 priority. With
+// the degree node order those are the most-read rows; the budget is
+// osp_options.l2_hot_bytes (default 60% of L2) over the bytes of one group's
+// row slice.
+int hot_rows(const osp_ctx* ctx, int precision, int KG) {
+  if (ctx->opt.node_order != 1 || ctx->opt.l2_hot_bytes < 0) return 0;
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    l2 = 0;
+  }
+  const int64_t budget = ctx->opt.l2_hot_bytes > 0 ? ctx->opt.l2_hot_bytes : (int64_t)l2 * 6 / 10;
+  const int elem = precision == OSP_PREC_FP64 ? 8 : precision == OSP_PREC_FP32_ACC64 ? 4 : 2;
+  const int64_t rows = budget / (32LL * KG * elem);
+  return (int)std::min<int64_t>(rows, ctx->nc);
 }
 
 // Seed block of K column groups computed in `precision`: stage source rows by
@@ -466,10 +516,11 @@ PropParams prop_params(osp_ctx* ctx, double eps) {
 // measured faster (Chung-Lu 2^22, 64 FP32 seeds: 4.16 vs 6.08 ms per pull
 // step); rows of 512 bytes (R-MAT 2^24, 256 bf16 seeds) ran slower (30.7 vs
 // 26.3 ms) and keep register gathers.
-bool seed_bulk(const osp_ctx* ctx, int precision, int K) {
+bool seed_bulk(const osp_ctx* ctx, int precision, int KG) {
   if (ctx->opt.seed_gather != 0) return ctx->opt.seed_gather == 2;
   const int elem = precision == OSP_PREC_FP64 ? 8 : precision == OSP_PREC_FP32_ACC64 ? 4 : 2;
-  return 32 * K * elem <= 256;
+  const int row = 32 * KG * elem;
+  return row >= 128 && row <= 256;
 }
 
 // The persistent propagation kernel of one call.
@@ -477,11 +528,13 @@ osp_status enqueue_propagate(osp_ctx* ctx, const PropParams& pp, bool init) {
   if (ctx->S > 1) {
     // bf16 gather vectors carry the small offsets of batches; the initial CPI
     // (total mass 1) runs with float gather vectors
-    const int prec = init && ctx->opt.precision == OSP_PREC_BF16_ACC64 ? (int)OSP_PREC_FP32_ACC64
-                                                                       : ctx->opt.precision;
-    CK(launch_propagate_multi(ctx->d, pp, prec, prec == ctx->opt.precision ? ctx->grid_multi
-                                                                             : ctx->grid_multi_init,
-                              seed_bulk(ctx, prec, ctx->d.mu.K), ctx->stream));
+    const bool as_init = init && ctx->opt.precision == OSP_PREC_BF16_ACC64;
+    const int prec = as_init ? (int)OSP_PREC_FP32_ACC64 : ctx->opt.precision;
+    const int KG = as_init ? ctx->d.mu.KG_init : ctx->d.mu.KG;
+    PropParams p = pp;
+    p.hot_n = hot_rows(ctx, prec, KG);
+    CK(launch_propagate_multi(ctx->d, p, prec, KG, as_init ? ctx->grid_multi_init : ctx->grid_multi,
+                              seed_bulk(ctx, prec, KG), ctx->stream));
   }
   else
     CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
@@ -687,6 +740,9 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
   return finish_call(ctx, m_before, st);
 }
 
+// Seed j's column of the seed block (the seed itself with one seed).
+int col_for(const osp_ctx* ctx, int j) { return ctx->S > 1 ? ctx->col_of[j] : j; }
+
 // Column col of the scores in caller order into dst, on stream st.
 osp_status enqueue_gather(osp_ctx* ctx, cudaStream_t st, int col, double* dst) {
   const int n = (int)ctx->n;
@@ -806,6 +862,13 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
   if (ctx->opt.seed_gather < 0 || ctx->opt.seed_gather > 2) {
     delete ctx;
     return OSP_EINVAL;
+  }
+  {
+    const int g = ctx->opt.seed_group;
+    if (g != 0 && g != 32 && g != 64 && g != 128 && g != 256) {
+      delete ctx;
+      return OSP_EINVAL;
+    }
   }
   ctx->device = ctx->opt.device;
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -1108,7 +1171,24 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     const size_t nh = (size_t)(ctx->cap_c / kMultiHub) + 2;
     unsigned char* y0 = nullptr;
     unsigned char* y1 = nullptr;
+    unsigned char* ebuf = nullptr;
     double* hub = nullptr;
+    // columns: seeds with out-edges first, then dead-end seeds (whose column
+    // has a zero offset unless a batch gives the seed out-edges), each part in
+    // the caller's order, so that column groups of dead-end seeds mostly skip
+    std::vector<int32_t> deg(S, 0);
+    for (int i = 0; i < S; ++i)
+      CK(cudaMemcpy(&deg[i], ctx->d.len_r + s_int[i], sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> order;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < S; ++i)
+        if ((deg[i] > 0) == (pass == 0)) order.push_back(i);
+    ctx->col_of.assign(S, 0);
+    std::vector<int32_t> by_col(S);
+    for (int c = 0; c < S; ++c) {
+      ctx->col_of[order[c]] = c;
+      by_col[c] = s_int[order[c]];
+    }
 #define ML(p, cnt)                                                    \
   do {                                                                \
     s = dalloc(ctx, &(p), (size_t)(cnt), 0, &ctx->mallocs);           \
@@ -1122,27 +1202,39 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     ML(M.xacc, cells);
     ML(y0, cells * ybytes);
     ML(y1, cells * ybytes);
+    if (ctx->opt.precision == OSP_PREC_BF16_ACC64) ML(ebuf, cells * 2);
     ML(M.part, (size_t)kMaxGrid * 32 * K);
     ML(M.active, 32 * K);
+    ML(M.touched, 32 * K);
     ML(M.col_iters, 32 * K);
     ML(M.col_q, 32 * K);
     ML(M.col_last, 32 * K);
+    ML(M.res_bound, 32 * K);
     ML(M.force, 32 * K);
     ML(hub, nh * 32 * K);
+    ML(M.hub_cnt, nh * 8);
 #undef ML
     M.S = S;
     M.K = K;
     M.Sp = 32 * K;
     M.y0 = y0;
     M.y1 = y1;
+    M.e = ebuf;
     M.hub_acc = hub;
-    CK(cudaMemcpyAsync(M.seeds, s_int.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, ctx->stream));
+    // column groups: 32 columns for bf16 gather rows (64-byte slices; measured
+    // 8 ms per pass at R-MAT 2^24 against 28.7 ms for one masked 256-column
+    // pass), else one group of all Sp columns, unless the options say
+    const int g = ctx->opt.seed_group > 0 ? ctx->opt.seed_group
+                  : ctx->opt.precision == OSP_PREC_BF16_ACC64 ? 32 : 32 * K;
+    M.KG = std::max(1, std::min(K, g / 32));
+    M.KG_init = ctx->opt.seed_group > 0 ? M.KG : K;
+    CK(cudaMemcpyAsync(M.seeds, by_col.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, ctx->stream));
     const int prec_init =
         ctx->opt.precision == OSP_PREC_FP64 ? OSP_PREC_FP64 : OSP_PREC_FP32_ACC64;
-    ctx->grid_multi = propagate_multi_grid(ctx->opt.precision, K, ctx->num_sms,
-                                           seed_bulk(ctx, ctx->opt.precision, K));
-    ctx->grid_multi_init =
-        propagate_multi_grid(prec_init, K, ctx->num_sms, seed_bulk(ctx, prec_init, K));
+    ctx->grid_multi = propagate_multi_grid(ctx->opt.precision, M.KG, ctx->num_sms,
+                                           seed_bulk(ctx, ctx->opt.precision, M.KG));
+    ctx->grid_multi_init = propagate_multi_grid(prec_init, M.KG_init, ctx->num_sms,
+                                                seed_bulk(ctx, prec_init, M.KG_init));
     if (ctx->grid_multi <= 0 || ctx->grid_multi_init <= 0) {
       free_multi(ctx);
       return fail(ctx, OSP_ECUDA, "no resident grid for the seed-block kernel");
@@ -1162,6 +1254,7 @@ osp_status enqueue_cpi_start(osp_ctx* ctx) {
   if (ctx->S > 1) {
     const Multi& M = ctx->d.mu;
     CK(cudaMemsetAsync(M.r, 0, sizeof(double) * (size_t)ctx->nc * M.Sp, ctx->stream));
+    CK(cudaMemsetAsync(M.res_bound, 0, sizeof(double) * M.Sp, ctx->stream));
     k_multi_cpi_begin<<<1, kMaxSeeds, 0, ctx->stream>>>(ctx->d);
   } else {
     CK(cudaMemsetAsync(ctx->d.r, 0, sizeof(double) * ctx->nc, ctx->stream));
@@ -1238,6 +1331,7 @@ osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
   }
   if (!ctx->qslots.empty()) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_queries, 0));
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  ctx->res_bound = 0.0;
   s = enqueue_cpi_start(ctx);
   if (s != OSP_OK) return s;
   s = run_propagation(ctx, eps, ctx->n, ctx->m, true);
@@ -1295,7 +1389,7 @@ osp_status osp_query_device(osp_ctx* ctx, int32_t seed_idx, int normalize, doubl
   if (s != OSP_OK) return s;
   if (seed_idx < 0 || seed_idx >= ctx->S || !out_device)
     return fail(ctx, OSP_EINVAL, "bad seed index or output");
-  s = scores_in_caller_order(ctx, seed_idx, normalize, out_device);
+  s = scores_in_caller_order(ctx, col_for(ctx, seed_idx), normalize, out_device);
   if (s != OSP_OK) return s;
   CK(cudaStreamSynchronize(ctx->stream));
   return OSP_OK;
@@ -1306,7 +1400,7 @@ osp_status osp_query(osp_ctx* ctx, int32_t seed_idx, int normalize, double* out)
   if (s != OSP_OK) return s;
   if (seed_idx < 0 || seed_idx >= ctx->S || !out)
     return fail(ctx, OSP_EINVAL, "bad seed index or output");
-  s = scores_in_caller_order(ctx, seed_idx, normalize, ctx->dtmp);
+  s = scores_in_caller_order(ctx, col_for(ctx, seed_idx), normalize, ctx->dtmp);
   if (s != OSP_OK) return s;
   CK(cudaMemcpyAsync(out, ctx->dtmp, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1321,7 +1415,7 @@ osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, in
     return fail(ctx, OSP_EINVAL, "bad seed index, k outside [1, 4096] or null output");
   cudaStream_t st = ctx->stream;
   // rank the scores in caller order, so that ties go to the smaller caller id
-  s = enqueue_gather(ctx, st, seed_idx, ctx->dtmp);
+  s = enqueue_gather(ctx, st, col_for(ctx, seed_idx), ctx->dtmp);
   if (s != OSP_OK) return s;
   const TopkScratch t{ctx->tk_state, ctx->tk_hist, ctx->tk_blk_a, ctx->tk_blk_b, ctx->tk_keys,
                       ctx->tk_ids, ctx->tk_out_ids, ctx->tk_out_sc, ctx->tk_out_k, ctx->dsum};
@@ -1389,7 +1483,7 @@ osp_status osp_topk_async(osp_ctx* ctx, int32_t slot, int32_t seed_idx, int32_t 
     return fail(ctx, OSP_EINVAL, "bad seed index or k outside [1, 4096]");
   cudaStream_t qs = ctx->qstream;
   CK(cudaStreamWaitEvent(qs, ctx->ev_scores, 0));
-  s = enqueue_gather(ctx, qs, seed_idx, q.col);
+  s = enqueue_gather(ctx, qs, col_for(ctx, seed_idx), q.col);
   if (s == OSP_OK) s = enqueue_topk(ctx, qs, q.col, (int)ctx->n, k, normalize, q.t);
   if (s != OSP_OK) return s;
   CK(cudaEventRecord(q.done, qs));
@@ -1480,10 +1574,19 @@ osp_status osp_get_seed_stats(osp_ctx* ctx, int32_t* iterations, double* qoff_l1
   cudaStream_t st = ctx->stream;
   if (ctx->S > 1) {
     const Multi& M = ctx->d.mu;
-    if (iterations && k)
-      CK(cudaMemcpyAsync(iterations, M.col_iters, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st));
-    if (qoff_l1 && k) CK(cudaMemcpyAsync(qoff_l1, M.col_q, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-    if (last_l1 && k) CK(cudaMemcpyAsync(last_l1, M.col_last, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    const int S = ctx->S;
+    std::vector<int32_t> it(S);
+    std::vector<double> q(S), last(S);
+    CK(cudaMemcpyAsync(it.data(), M.col_iters, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(q.data(), M.col_q, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(last.data(), M.col_last, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < k; ++j) {
+      const int c = ctx->col_of[j];
+      if (iterations) iterations[j] = it[c];
+      if (qoff_l1) qoff_l1[j] = q[c];
+      if (last_l1) last_l1[j] = last[c];
+    }
   } else if (k > 0) {
     if (iterations) iterations[0] = ctx->last_iters;
     const int last = std::min(ctx->last_iters, kMaxHist - 1);
@@ -1516,12 +1619,34 @@ osp_status osp_set_seed_iterations(osp_ctx* ctx, const int32_t* k, int32_t S) {
   CK(cudaSetDevice(ctx->device));
   const Multi& M = ctx->d.mu;
   std::vector<int32_t> f(M.Sp, 0);
-  for (int j = 0; k && j < S; ++j) f[j] = k[j];
+  for (int j = 0; k && j < S; ++j) f[ctx->col_of[j]] = k[j];
   int mx = 0;
   for (int v : f) mx = std::max(mx, v);
   ctx->seed_force_max = mx;
   CK(cudaMemcpyAsync(M.force, f.data(), sizeof(int32_t) * M.Sp, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return OSP_OK;
+}
+
+int64_t osp_num_nodes(const osp_ctx* ctx) { return ctx ? ctx->n : -1; }
+
+int64_t osp_device_bytes(const osp_ctx* ctx) { return ctx ? ctx->hbm_used : -1; }
+
+osp_status osp_get_residual_bounds(osp_ctx* ctx, double* out, int32_t cap, int32_t* count) {
+  if (!ctx || !out || !count || cap < 0) return OSP_EINVAL;
+  if (!ctx->seeded) return fail(ctx, OSP_ESTATE, "no seed set");
+  CK(cudaSetDevice(ctx->device));
+  const int k = std::min<int>(ctx->S, cap);
+  if (ctx->S > 1) {
+    std::vector<double> rb(ctx->S);
+    CK(cudaMemcpyAsync(rb.data(), ctx->d.mu.res_bound, sizeof(double) * ctx->S,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < k; ++j) out[j] = rb[ctx->col_of[j]];
+  } else if (k > 0) {
+    out[0] = ctx->res_bound;
+  }
+  *count = k;
   return OSP_OK;
 }
 

@@ -57,9 +57,9 @@ __global__ void k_multi_cpi_begin(Dev d);
 __global__ void k_gather_col(const double* __restrict__ r, int Sp, int col,
                              const int* __restrict__ ext2int, int n, double* out);
 // bulk: the variant that stages source rows in shared memory by bulk copies.
-int propagate_multi_grid(int precision, int K, int num_sms, bool bulk);
-cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int grid,
-                                   bool bulk, cudaStream_t s);
+int propagate_multi_grid(int precision, int KG, int num_sms, bool bulk);
+cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int KG,
+                                   int grid, bool bulk, cudaStream_t s);
 cudaError_t launch_offset_multi(const Dev& d, int grid, cudaStream_t s);
 // Failure-detection self-test: which 0 = grid barrier, 1 = staged-row mbarrier;
 // lose != 0 makes the wait run out (src: 64 floats on the device).

@@ -71,50 +71,256 @@ __device__ __forceinline__ void store_k(T* p, const T (&v)[K]) {
   }
 }
 
-// Per-column |x| partials of this CTA: lanes hold their K columns; warps are
-// combined in shared memory in a fixed order.
-template <int K>
-__device__ __forceinline__ void column_partials(const Multi& M, const double (&l1)[K],
-                                                double* s_part) {
-  constexpr int Sp = 32 * K;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// ---------------------------------------------------------------------------
+// L2 eviction priorities. Source rows of the gather block whose internal id is
+// below PropParams::hot_n (with the degree node order: the most-read rows) are
+// loaded with evict_last, so that they stay in L2 across a pull step; every
+// other access of the step (cold source rows, score rows, residuals, the next
+// gather block) touches its line once per step and is marked evict_first.
+// All accesses go through L2 only (.cg): the gather blocks and score rows are
+// rewritten inside the same persistent kernel.
+// ---------------------------------------------------------------------------
+struct L2Pol {
+  unsigned long long keep;    // evict_last
+  unsigned long long once;    // evict_first
+  unsigned long long normal;  // evict_normal
+};
+
+__device__ __forceinline__ L2Pol make_l2pol() {
+  L2Pol p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.once));
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p.normal));
+  return p;
+}
+
+// K contiguous elements (K * sizeof(T) bytes, naturally aligned) through L2
+// with an eviction policy.
+template <typename T, int K>
+__device__ __forceinline__ void ld_pol(const T* p, T (&out)[K], unsigned long long pol) {
+  constexpr int B = K * (int)sizeof(T);
+  static_assert(B == 2 || B == 4 || B == 8 || B % 16 == 0, "row slice size");
+  if constexpr (B >= 16) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) s_part[w * Sp + lane * K + k] = l1[k];
-  __syncthreads();
-  for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
-    double a = 0.0;
-    for (int i = 0; i < kPropWarps; ++i) a += s_part[i * Sp + j];
-    M.part[(size_t)blockIdx.x * Sp + j] = a;
+    for (int i = 0; i < B / 16; ++i) {
+      uint4 v;
+      asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                   : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                   : "l"(reinterpret_cast<const uint4*>(p) + i), "l"(pol));
+      reinterpret_cast<uint4*>(out)[i] = v;
+    }
+  } else if constexpr (B == 8) {
+    uint2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p), "l"(pol));
+    *reinterpret_cast<uint2*>(out) = v;
+  } else if constexpr (B == 4) {
+    unsigned v;
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    *reinterpret_cast<unsigned*>(out) = v;
+  } else {
+    unsigned short v;
+    asm volatile("ld.global.cg.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    *reinterpret_cast<unsigned short*>(out) = v;
   }
-  __threadfence();
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void st_pol(T* p, const T (&val)[K], unsigned long long pol) {
+  constexpr int B = K * (int)sizeof(T);
+  static_assert(B == 2 || B == 4 || B == 8 || B % 16 == 0, "row slice size");
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i) {
+      const uint4 v = reinterpret_cast<const uint4*>(val)[i];
+      asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(
+                       reinterpret_cast<uint4*>(p) + i),
+                   "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+                   : "memory");
+    }
+  } else if constexpr (B == 8) {
+    const uint2 v = *reinterpret_cast<const uint2*>(val);
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "l"(pol)
+                 : "memory");
+  } else if constexpr (B == 4) {
+    const unsigned v = *reinterpret_cast<const unsigned*>(val);
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+  } else {
+    const unsigned short v = *reinterpret_cast<const unsigned short*>(val);
+    asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(p), "h"(v), "l"(pol) : "memory");
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void zero_k(T (&out)[K]) {
+  constexpr int B = K * (int)sizeof(T);
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i) reinterpret_cast<uint4*>(out)[i] = make_uint4(0, 0, 0, 0);
+  } else if constexpr (B == 8) {
+    *reinterpret_cast<uint2*>(out) = make_uint2(0, 0);
+  } else if constexpr (B == 4) {
+    *reinterpret_cast<unsigned*>(out) = 0u;
+  } else {
+    *reinterpret_cast<unsigned short*>(out) = 0;
+  }
+}
+
+// bf16 gather rows carry the rounding residual of each stored value into the
+// next step's rounding (error feedback, below); float and double rows do not.
+template <typename TY> struct Feedback { static constexpr bool on = false; };
+template <> struct Feedback<__nv_bfloat16> { static constexpr bool on = true; };
+
+// Registers of one warp lane: KG columns of one column group.
+template <typename TY, int KG>
+struct ColGroup {
+  static constexpr int G = 32 * KG;                      // columns of a group
+  static constexpr int kRowBytes = G * (int)sizeof(TY);  // a group's slice of a gather row
+  // rows gathered per batch of loads (more when a lane's share is small)
+  static constexpr int kDepth = KG * (int)sizeof(TY) <= 8 ? 16 : 8;
+};
+
+// Sum of the gather rows of in-list entries p[0 .. len) into acc (this lane's
+// KG columns; ys points at the lane's first column of row 0 of the group, rows
+// Sp elements apart): 32 ids per coalesced load, then kDepth rows in flight.
+template <typename TY, int KG, typename A>
+__device__ __forceinline__ void sum_rows(const int* p, int len, const TY* ys, int Sp, A (&acc)[KG],
+                                         int idx0, const L2Pol& pol, unsigned long long cold,
+                                         int hot_n, bool on) {
+  constexpr int D = ColGroup<TY, KG>::kDepth;
+  const int lane = threadIdx.x & 31;
+  for (int b = 0; b < len; b += 32) {
+    const int cnt = min(32, len - b);
+    // ids of the first block may come preloaded (idx0 >= 0 on every lane)
+    const int idx = (b == 0 && __all_sync(0xffffffffu, idx0 >= 0)) ? idx0
+                    : (lane < cnt ? __ldg(p + b + lane) : 0);
+    int j = 0;
+    for (; j + D <= cnt; j += D) {
+      alignas(16) TY a[D][KG];
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const int u = __shfl_sync(0xffffffffu, idx, j + q);
+        if (on) ld_pol(ys + (size_t)u * Sp, a[q], u < hot_n ? pol.keep : cold);
+        else zero_k(a[q]);
+      }
+#pragma unroll
+      for (int k = 0; k < KG; ++k) {
+        A t[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) t[q] = to_acc(a[q][k]);
+#pragma unroll
+        for (int h = D / 2; h > 0; h >>= 1)
+#pragma unroll
+          for (int q = 0; q < h; ++q) t[q] += t[q + h];
+        acc[k] += t[0];
+      }
+    }
+    for (; j + 4 <= cnt; j += 4) {
+      alignas(16) TY a[4][KG];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = __shfl_sync(0xffffffffu, idx, j + q);
+        if (on) ld_pol(ys + (size_t)u * Sp, a[q], u < hot_n ? pol.keep : cold);
+        else zero_k(a[q]);
+      }
+#pragma unroll
+      for (int k = 0; k < KG; ++k)
+        acc[k] += (to_acc(a[0][k]) + to_acc(a[1][k])) + (to_acc(a[2][k]) + to_acc(a[3][k]));
+    }
+    for (; j < cnt; ++j) {
+      const int u = __shfl_sync(0xffffffffu, idx, j);
+      alignas(16) TY a[KG];
+      if (on) ld_pol(ys + (size_t)u * Sp, a, u < hot_n ? pol.keep : cold);
+      else zero_k(a);
+#pragma unroll
+      for (int k = 0; k < KG; ++k) acc[k] += to_acc(a[k]);
+    }
+  }
+}
+
+// x(i)[v] of this lane's KG columns of one group is acc. base / ybase: offset
+// of the lane's first column in row v of R / of the group's gather block. rr: the row of R (loaded when the in-list is
+// nonempty); eo: the carried residuals (bf16 rows). The running columns add x
+// into R and |x| into l1; a node with out-edges (s != 0) writes its next
+// gather row. With bf16 rows the value stored is the rounding of
+// w = x s + e_old and the new residual is e = w - stored (error feedback:
+// the stored values' rounding errors then telescope instead of adding up).
+template <typename TY, int KG, typename A>
+__device__ __forceinline__ void finish_slice(const Multi& M, size_t base, size_t ybase,
+                                             const A (&acc)[KG], A s, bool has_in, double (&rr)[KG],
+                                             const TY (&eo)[KG], unsigned act, TY* yd,
+                                             double (&l1)[KG], const L2Pol& pol) {
+  // a lane whose columns have all stopped moves nothing: its score entries
+  // stay, and its gather entries are not read again in this call
+  if (!act) return;
+  if (has_in) {
+#pragma unroll
+    for (int k = 0; k < KG; ++k)
+      if (act & (1u << k)) {
+        const double x = (double)acc[k];
+        rr[k] += x;
+        l1[k] += fabs(x);
+      }
+    st_pol(M.r + base, rr, pol.once);
+  }
+  if (s != (A)0) {
+    alignas(16) TY yv[KG];
+    if constexpr (Feedback<TY>::on) {
+      alignas(16) TY ev[KG];
+#pragma unroll
+      for (int k = 0; k < KG; ++k) {
+        const float w = (float)(acc[k] * s) + __bfloat162float(eo[k]);
+        yv[k] = __float2bfloat16_rn(w);
+        ev[k] = __float2bfloat16_rn(w - __bfloat162float(yv[k]));
+      }
+      st_pol(reinterpret_cast<TY*>(M.e) + ybase, ev, pol.once);
+    } else {
+#pragma unroll
+      for (int k = 0; k < KG; ++k) yv[k] = from_acc((A)(acc[k] * s), (TY*)nullptr);
+    }
+    st_pol(yd + ybase, yv, pol.once);
+  }
+}
+
+template <typename A>
+__device__ __forceinline__ A scale_of(const Dev& d, int v) {
+  return std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
 }
 
 // Whole last CTA: per-column sums of the partials (fixed order over CTAs),
-// per-column stopping, the call's stop and the history entry (max over the
-// columns that ran the step).
-template <int K>
+// per-column stopping, the call's stop, the column groups still running and
+// the history entry (max over the columns that ran the step). A column whose
+// x(0) is exactly zero has only zero terms: under the eps rule its one
+// do-while step is counted and it stops at once.
+template <int KG>
 __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long long m) {
-  constexpr int Sp = 32 * K;
+  constexpr int G = 32 * KG;
   const Multi& M = d.mu;
+  const int Sp = M.Sp;
   Ctl* ctl = d.ctl;
   __shared__ double s_max[kPropThreads / 32];
   __shared__ double s_sum[kPropThreads];
+  __shared__ unsigned s_gmask;
+  if (threadIdx.x == 0) s_gmask = 0;
   // thread t sums column t % Sp over the CTAs b = t / Sp (mod Q) with eight
   // independent accumulators; the Q slices are then added in a fixed order
   const int Q = (int)blockDim.x / Sp;
-  const int G = (int)gridDim.x;
+  const int GR = (int)gridDim.x;
   {
     const int jc = threadIdx.x % Sp, q = threadIdx.x / Sp;
     double a[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) a[u] = 0.0;
-    for (int b = q; b < G; b += 8 * Q) {
+    if (q < Q)
+      for (int b = q; b < GR; b += 8 * Q) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int bb = b + u * Q;
-        if (bb < G) a[u] += __ldcg(M.part + (size_t)bb * Sp + jc);
+        for (int u = 0; u < 8; ++u) {
+          const int bb = b + u * Q;
+          if (bb < GR) a[u] += __ldcg(M.part + (size_t)bb * Sp + jc);
+        }
       }
-    }
     s_sum[threadIdx.x] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
   __syncthreads();
@@ -124,25 +330,38 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
     double L = 0.0;
     for (int q = 0; q < Q; ++q) L += s_sum[q * Sp + j];
     if (j >= M.S) continue;
+    const int f = pp.force_iters > 0 ? pp.force_iters : M.force[j];
     if (it == 0) {
       M.col_q[j] = L;
       M.col_last[j] = L;
-      M.col_iters[j] = 0;
-      M.active[j] = 1;
+      M.touched[j] = 0;  // the next offset marks its columns again
       seen = fmax(seen, L);
-      live = 1;
+      if (L == 0.0 && f == 0) {
+        M.col_iters[j] = 1;
+        M.active[j] = 0;
+      } else {
+        M.col_iters[j] = 0;
+        M.active[j] = 1;
+        live = 1;
+        atomicOr(&s_gmask, 1u << (j / G));
+      }
     } else if (*(volatile int*)&M.active[j]) {
       M.col_iters[j] = it;
       M.col_last[j] = L;
       seen = fmax(seen, L);
-      const int f = pp.force_iters > 0 ? pp.force_iters : M.force[j];
       int stop = f > 0 ? it >= f : L <= pp.eps;
       if (!stop && it >= pp.max_iter) {
         stop = 1;
         ctl->noconv = 1;
       }
-      if (stop) M.active[j] = 0;
-      else live = 1;
+      if (stop) {
+        M.active[j] = 0;
+        // the untaken tail's residual x(k+1) has norm <= (1-c) ||x(k)||_1
+        M.res_bound[j] += (1.0 - ctl->c) * L;
+      } else {
+        live = 1;
+        atomicOr(&s_gmask, 1u << (j / G));
+      }
     }
   }
   seen = warp_max(seen);
@@ -156,90 +375,22 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
       d.step_ns[it + 1] = global_ns();
     }
     ctl->iter = it;
+    if (it == 0 && !any && kMaxHist > 1) {
+      // every x(0) is zero: the do-while's single step is x(1) = 0
+      d.l1_hist[1] = 0.0;
+      d.step_ns[2] = d.step_ns[1];
+      ctl->iter = 1;
+    }
     if (it > 0) {
       ctl->visited += m;
       ctl->pull_used = 1;
     }
+    int ng = 0;
+    for (int g = 0; g < 8; ++g)
+      if (s_gmask & (1u << g)) ctl->grp[ng++] = g;
+    ctl->n_grp = ng;
     ctl->stop = !any;
     for (int i = 0; i < 4; ++i) ctl->ctr[i] = 0;
-  }
-}
-
-// x(i)[v] from the K-column sums acc: add into R for running columns (rr is
-// the row of R, loaded before the sums), write the next gather row (zero for
-// stopped columns), accumulate |x|.
-template <typename TY, int K, typename A>
-__device__ __forceinline__ void finish_row(const Dev& d, int v, const A (&acc)[K], A s,
-                                           double (&rr)[K], unsigned act, TY* yd,
-                                           double (&l1)[K]) {
-  constexpr int Sp = 32 * K;
-  const int lane = threadIdx.x & 31;
-  const size_t base = (size_t)v * Sp + lane * K;
-  alignas(16) TY yv[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (act & (1u << k)) {
-      const double x = (double)acc[k];
-      rr[k] += x;
-      l1[k] += fabs(x);
-      yv[k] = from_acc((A)(acc[k] * s), (TY*)nullptr);
-    } else {
-      yv[k] = from_acc((A)0, (TY*)nullptr);
-    }
-  }
-  store_k(d.mu.r + base, rr);
-  store_k(yd + base, yv);
-}
-
-template <typename A>
-__device__ __forceinline__ A scale_of(const Dev& d, int v) {
-  return std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
-}
-
-// Sum of y rows over in-list entries p[0 .. len): 32 ids per coalesced load,
-// then up to eight rows in flight.
-template <typename TY, int K, typename A>
-__device__ __forceinline__ void sum_rows(const int* p, int len, const TY* ys, A (&acc)[K],
-                                         int idx0 = -1) {
-  constexpr int Sp = 32 * K;
-  const int lane = threadIdx.x & 31;
-  for (int b = 0; b < len; b += 32) {
-    const int cnt = min(32, len - b);
-    // ids of the first block may come preloaded (idx0 >= 0 on every lane)
-    const int idx = (b == 0 && __all_sync(0xffffffffu, idx0 >= 0)) ? idx0
-                    : (lane < cnt ? __ldg(p + b + lane) : 0);
-    int j = 0;
-    for (; j + 8 <= cnt; j += 8) {
-      alignas(16) TY a[8][K];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int u = __shfl_sync(0xffffffffu, idx, j + q);
-        load_cg(ys + (size_t)u * Sp + lane * K, a[q]);
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        acc[k] += ((to_acc(a[0][k]) + to_acc(a[1][k])) + (to_acc(a[2][k]) + to_acc(a[3][k]))) +
-                  ((to_acc(a[4][k]) + to_acc(a[5][k])) + (to_acc(a[6][k]) + to_acc(a[7][k])));
-    }
-    if (j + 4 <= cnt) {
-      alignas(16) TY a[4][K];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int u = __shfl_sync(0xffffffffu, idx, j + q);
-        load_cg(ys + (size_t)u * Sp + lane * K, a[q]);
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        acc[k] += (to_acc(a[0][k]) + to_acc(a[1][k])) + (to_acc(a[2][k]) + to_acc(a[3][k]));
-      j += 4;
-    }
-    for (; j < cnt; ++j) {
-      const int u = __shfl_sync(0xffffffffu, idx, j);
-      alignas(16) TY a[K];
-      load_cg(ys + (size_t)u * Sp + lane * K, a);
-#pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] += to_acc(a[k]);
-    }
   }
 }
 
@@ -322,9 +473,22 @@ __device__ __forceinline__ void bulk_copy_row(unsigned dst, const void* src, uns
       : "memory");
 }
 
-// Rows u (lane j < cnt holds row j's id) of the gather block into buffer b.
+// The same with an L2 eviction policy for the source line(s).
+__device__ __forceinline__ void bulk_copy_row_pol(unsigned dst, const void* src, unsigned bytes,
+                                                  unsigned bar, unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], "
+      "%2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+
+// Rows u (lane j < cnt holds row j's id) of one column group of the gather
+// block (rows of 32 K elements, contiguous: ys is the group's row 0) into
+// buffer b.
 template <typename TY, int K>
-__device__ __forceinline__ void ring_issue(const Ring& rg, int b, int cnt, int u, const TY* ys) {
+__device__ __forceinline__ void ring_issue(const Ring& rg, int b, int cnt, int u, const TY* ys,
+                                           const L2Pol& pol, unsigned long long cold, int hot_n) {
   using C = RingCfg<TY, K>;
   const int lane = threadIdx.x & 31;
   const unsigned bar = rg.bar + 8u * (unsigned)b;
@@ -333,8 +497,9 @@ __device__ __forceinline__ void ring_issue(const Ring& rg, int b, int cnt, int u
   if (lane == 0) mbar_arrive_expect(bar, (unsigned)(cnt * C::kRowBytes));
   __syncwarp();
   if (lane < cnt)
-    bulk_copy_row(rg.rows + (unsigned)((b * C::kRows + lane) * C::kRowBytes),
-                  ys + (size_t)u * (32 * K), (unsigned)C::kRowBytes, bar);
+    bulk_copy_row_pol(rg.rows + (unsigned)((b * C::kRows + lane) * C::kRowBytes),
+                      ys + (size_t)u * (32 * K), (unsigned)C::kRowBytes, bar,
+                      u < hot_n ? pol.keep : cold);
 }
 
 // Wait for buffer b's batch. Bounded: after 2 s the call's status becomes
@@ -415,7 +580,7 @@ __device__ __forceinline__ void ring_sum(const Ring& rg, int b, int cnt, A (&acc
 // batches of kRows, two batches in flight.
 template <typename TY, int K, typename A>
 __device__ void ring_sum_list(Ring& rg, const Dev& d, const int* p, int L, const TY* ys,
-                              A (&acc)[K]) {
+                              A (&acc)[K], const L2Pol& pol, unsigned long long cold, int hot_n) {
   constexpr int G = RingCfg<TY, K>::kRows;
   const int lane = threadIdx.x & 31;
   auto ids = [&](int s0) -> int {
@@ -425,9 +590,9 @@ __device__ void ring_sum_list(Ring& rg, const Dev& d, const int* p, int L, const
     return u;
   };
   int b = rg.buf;
-  ring_issue<TY, K>(rg, b, min(G, L), ids(0), ys);
+  ring_issue<TY, K>(rg, b, min(G, L), ids(0), ys, pol, cold, hot_n);
   for (int s0 = 0; s0 < L; s0 += G) {
-    if (s0 + G < L) ring_issue<TY, K>(rg, b ^ 1, min(G, L - s0 - G), ids(s0 + G), ys);
+    if (s0 + G < L) ring_issue<TY, K>(rg, b ^ 1, min(G, L - s0 - G), ids(s0 + G), ys, pol, cold, hot_n);
     ring_wait(rg, b, d.ctl);
     ring_sum<TY, K, A>(rg, b, min(G, L - s0), acc);
     b ^= 1;
@@ -496,6 +661,7 @@ __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned hit = 0;  // bit k: this lane added a nonzero term to its column k
   for (int p = gw; p < np; p += nw) {
     const int c = d.piece_rec[p];
     const int q = p - d.rec_pstart[c];
@@ -536,11 +702,19 @@ __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
         double* row = d.mu.xacc + (size_t)aj * Sp + lane * K;
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          if (ru[k] != 0.0) atomicAdd(row + k, wj * ru[k]);
+          if (ru[k] != 0.0) {
+            atomicAdd(row + k, wj * ru[k]);
+            hit |= 1u << k;
+          }
         if (lane == 0) d.mark[aj] = epoch;
       }
     }
   }
+  // columns with a nonzero offset entry run this call's steps (the others
+  // have x(i) = 0 for every i)
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (hit & (1u << k)) d.mu.touched[lane * K + k] = 1;
 }
 
 // CPI start for every column: x(0) = c e_{s_j} in column j.
@@ -550,6 +724,7 @@ __global__ void k_multi_cpi_begin(Dev d) {
   if (j < M.S) {
     const int s = M.seeds[j];
     M.xacc[(size_t)s * M.Sp + j] = d.ctl->c;
+    M.touched[j] = 1;
     d.mark[s] = d.ctl->epoch;
   }
 }
@@ -561,21 +736,41 @@ __global__ void k_gather_col(const double* __restrict__ r, int Sp, int col,
     out[i] = r[(size_t)ext2int[i] * Sp + col];
 }
 
-// kBulk: short and medium in-lists stage whole source rows in shared memory
-// by bulk asynchronous copies (dynamic shared memory RingCfg<TY, K>::kSmem);
-// else each lane gathers its columns of up to eight rows into registers.
-template <typename TY, int K, bool kBulk>
-__global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, PropParams pp) {
+// CTAs per SM the seed-block kernel is built for: three when a lane's share
+// of a gather row is at most 4 bytes (few registers), else two.
+template <typename TY, int KG>
+struct MultiOcc {
+  static constexpr int value = KG * (int)sizeof(TY) <= 4 ? 3 : 2;
+};
+
+// The seed block, one persistent cooperative launch per call: the x(0) pass
+// and every pull step. Columns are processed in groups of G = 32 KG (lane l
+// owns columns [KG l, KG l + KG) of the group); a pull step walks its work
+// items once per group that still has a running column, group after group,
+// so the gathered rows of one group share L2 while it is walked, and groups
+// whose columns have all stopped cost nothing. The gather blocks (and the
+// bf16 residuals) are laid out group-major, [group][node][G], so that a
+// group's row is one contiguous slice of G elements; R is [node][Sp].
+// kBulk: in-lists stage their source rows in shared memory by bulk
+// asynchronous copies (dynamic shared memory RingCfg<TY, KG>::kSmem); else
+// each lane gathers its columns of up to kDepth rows into registers.
+template <typename TY, int KG, bool kBulk>
+__global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
+    k_propagate_multi(Dev d, PropParams pp) {
   using A = typename AccOf<TY>::type;
-  constexpr int Sp = 32 * K;
+  constexpr int G = 32 * KG;
+  constexpr bool FB = Feedback<TY>::on;
   __shared__ BarShared sh;
-  __shared__ double s_part[kPropWarps * Sp];
+  __shared__ double s_part[kPropWarps * kMaxSeeds];  // per warp, per column |x| sums
+  __shared__ int s_grp[8];
+  __shared__ int s_ngrp;
+  __shared__ unsigned s_tmask;
   extern __shared__ __align__(128) unsigned char dsm[];
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
   Ring rg{};
   if constexpr (kBulk) {
-    using C = RingCfg<TY, K>;
+    using C = RingCfg<TY, KG>;
     const int w = threadIdx.x >> 5;
     rg.bar = smem_u32(dsm) + 16u * (unsigned)w;
     const int off = C::kBarBytes + w * 2 * C::kRows * C::kRowBytes;
@@ -589,6 +784,8 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
     __syncthreads();
   }
   const Multi& M = d.mu;
+  const int Sp = M.Sp;
+  const size_t gs = (size_t)d.nc * G;  // gather block: elements per column group
   const int n = ctl->n;
   const long long m = ctl->m;
   const int epoch = ctl->epoch;
@@ -596,144 +793,242 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
   const int n_pieces = ctl->n_pieces;
   const int n_tasks = ctl->n_tasks;
   const int hub_thr = ctl->hub_thr, hub_piece = ctl->hub_piece;
+  const L2Pol pol = make_l2pol();
+  const int hot_n = pp.hot_n;
+  const unsigned long long cold = hot_n > 0 ? pol.once : pol.normal;
   TY* yb[2] = {(TY*)M.y0, (TY*)M.y1};
-  const int lane = threadIdx.x & 31;
+  TY* eb = (TY*)M.e;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  double* my_part = s_part + wid * kMaxSeeds;
   if (blockIdx.x == 0 && threadIdx.x == 0) d.step_ns[0] = global_ns();
 
-  // x(0): stamped rows from xacc into R and y(0); other rows of y(0) are zero
-  {
-    double l1[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) l1[k] = 0.0;
-    for (int vb = gw * 32; vb < n; vb += nw * 32) {
-     const int vl = vb + lane;
-     const unsigned stamped = __ballot_sync(0xffffffffu, vl < n && __ldcg(d.mark + vl) == epoch);
-     const int cnt = min(32, n - vb);
-     for (int jj = 0; jj < cnt; ++jj) {
-      const int v = vb + jj;
-      const size_t base = (size_t)v * Sp + lane * K;
-      alignas(16) TY yv[K];
-      if ((stamped >> jj) & 1u) {
-        alignas(16) double x[K], rr[K], z[K];
-        load_cg(M.xacc + base, x);
-        load_cg(M.r + base, rr);
-        const A s = scale_of<A>(d, v);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          rr[k] += x[k];
-          l1[k] += fabs(x[k]);
-          yv[k] = from_acc((A)((A)x[k] * s), (TY*)nullptr);
-          z[k] = 0.0;
-        }
-        store_k(M.r + base, rr);
-        store_k(M.xacc + base, z);
-      } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k) yv[k] = from_acc((A)0, (TY*)nullptr);
-      }
-      store_k(yb[0] + base, yv);
-     }
+  // per-CTA column sums of the warps' partials (fixed order) into M.part
+  auto column_sums = [&]() {
+    __syncthreads();
+    for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
+      double a = 0.0;
+      for (int i = 0; i < kPropWarps; ++i) a += s_part[i * kMaxSeeds + j];
+      M.part[(size_t)blockIdx.x * Sp + j] = a;
     }
-    column_partials<K>(M, l1, s_part);
-    if (bar_arrive(ctl, sh)) decide_multi<K>(d, pp, 0, m);
+    __threadfence();
+  };
+
+  // x(0): stamped rows move from xacc into R and, scaled, into y(0); every
+  // node with out-edges gets its y(0) row (zero when not stamped) in each
+  // column group that has a nonzero offset entry
+  {
+    if (threadIdx.x == 0) s_tmask = 0;
+    for (int j = lane; j < Sp; j += 32) my_part[j] = 0.0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < Sp && j < M.S; j += blockDim.x)
+      if (*(volatile int*)&M.touched[j]) atomicOr(&s_tmask, 1u << (j / G));
+    __syncthreads();
+    const unsigned tmask = s_tmask;
+    unsigned lane_touch = 0;  // bit g: one of this lane's columns in group g has an offset entry
+    for (unsigned tm = tmask; tm; tm &= tm - 1) {
+      const int g = __ffs(tm) - 1;
+      for (int k = 0; k < KG; ++k) {
+        const int j = g * G + lane * KG + k;
+        if (j < M.S && *(volatile int*)&M.touched[j]) lane_touch |= 1u << g;
+      }
+    }
+    for (int vb = gw * 32; vb < n && tmask; vb += nw * 32) {
+      const int vl = vb + lane;
+      const unsigned stamped = __ballot_sync(0xffffffffu, vl < n && __ldcg(d.mark + vl) == epoch);
+      const A s_l = vl < n ? scale_of<A>(d, vl) : (A)0;
+      unsigned work = stamped | __ballot_sync(0xffffffffu, s_l != (A)0);
+      while (work) {
+        const int jj = __ffs(work) - 1;
+        work &= work - 1;
+        const int v = vb + jj;
+        const bool st = (stamped >> jj) & 1u;
+        const A s = __shfl_sync(0xffffffffu, s_l, jj);
+        for (unsigned tm = tmask; tm; tm &= tm - 1) {
+          const int g = __ffs(tm) - 1;
+          if (!((lane_touch >> g) & 1u)) continue;  // none of this lane's columns has an offset
+          const size_t rbase = (size_t)v * Sp + g * G + lane * KG;
+          const size_t ybase = g * gs + (size_t)v * G + lane * KG;
+          alignas(16) TY yv[KG];
+          alignas(16) TY ev[KG];
+          if (st) {
+            alignas(16) double x[KG], rr[KG], z[KG];
+            ld_pol(M.xacc + rbase, x, pol.once);
+            ld_pol(M.r + rbase, rr, pol.once);
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+              rr[k] += x[k];
+              my_part[g * G + lane * KG + k] += fabs(x[k]);
+              z[k] = 0.0;
+              const A w = (A)((A)x[k] * s);
+              yv[k] = from_acc(w, (TY*)nullptr);
+              if constexpr (FB) ev[k] = __float2bfloat16_rn(w - __bfloat162float(yv[k]));
+            }
+            st_pol(M.r + rbase, rr, pol.once);
+            st_pol(M.xacc + rbase, z, pol.once);
+          } else {
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+              yv[k] = from_acc((A)0, (TY*)nullptr);
+              ev[k] = yv[k];
+            }
+          }
+          if (s != (A)0) {
+            st_pol(yb[0] + ybase, yv, pol.once);
+            if constexpr (FB) st_pol(eb + ybase, ev, pol.once);
+          }
+        }
+      }
+    }
+    column_sums();
+    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, 0, m);
     if (!bar_release(ctl, sh)) return;
   }
 
   A* hub_acc = (A*)M.hub_acc;
   for (int it = 1;; ++it) {
     if (*(volatile int*)&ctl->stop) break;
-    unsigned act = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) act |= (unsigned)(*(volatile int*)&M.active[lane * K + k] != 0) << k;
+    if (threadIdx.x < 8) s_grp[threadIdx.x] = *(volatile int*)&ctl->grp[threadIdx.x];
+    if (threadIdx.x == 0) s_ngrp = *(volatile int*)&ctl->n_grp;
+    for (int j = lane; j < Sp; j += 32) my_part[j] = 0.0;
+    __syncthreads();
     const TY* ys = yb[(it - 1) & 1];
     TY* yd = yb[it & 1];
-    double l1[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) l1[k] = 0.0;
     const int n_items = n_pieces + n_tasks;
+    const long long total = (long long)s_ngrp * n_items;
+    int cur = -1;  // column group of the items this warp works on now
+    unsigned act = 0;
+    double l1[KG];
+#pragma unroll
+    for (int k = 0; k < KG; ++k) l1[k] = 0.0;
+    auto flush = [&]() {
+      if (cur >= 0) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          my_part[cur * G + lane * KG + k] += l1[k];
+          l1[k] = 0.0;
+        }
+      }
+    };
     for (;;) {
       int t = 0;
       if (lane == 0) t = atomicAdd(&ctl->ctr[1], 1);
       t = __shfl_sync(0xffffffffu, t, 0);
-      if (t >= n_items) break;
-      if (t < n_pieces) {
+      if (t >= total) break;
+      const int gi = t / n_items;
+      const int ti = t - gi * n_items;
+      const int g = s_grp[gi];
+      if (g != cur) {
+        flush();
+        cur = g;
+        act = 0;
+#pragma unroll
+        for (int k = 0; k < KG; ++k)
+          act |= (unsigned)(*(volatile int*)&M.active[g * G + lane * KG + k] != 0) << k;
+      }
+      const TY* ysg = ys + g * gs;           // the group's gather rows, G elements apart
+      const TY* ysl = ysg + lane * KG;       // this lane's columns of them
+      const size_t c0 = (size_t)g * G + lane * KG;
+      auto rbase_of = [&](int v) { return (size_t)v * Sp + c0; };
+      auto ybase_of = [&](int v) { return g * gs + (size_t)v * G + lane * KG; };
+      if (ti < n_pieces) {
         // a piece of a long in-list; the piece that completes the list finishes it
         int lo = 0, hi = n_hubs;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (__ldg(d.hub_pstart + mid) <= t) lo = mid;
+          if (__ldg(d.hub_pstart + mid) <= ti) lo = mid;
           else hi = mid;
         }
         const int h = lo;
         const int v = __ldg(d.hubs + h);
-        const int piece = t - __ldg(d.hub_pstart + h);
+        const int piece = ti - __ldg(d.hub_pstart + h);
         const int full = __ldg(d.len_c + v);
         const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * hub_piece);
         const int L = min(hub_piece, full - piece * hub_piece);
-        A acc[K];
+        A acc[KG];
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = (A)0;
-        if constexpr (kBulk) ring_sum_list<TY, K, A>(rg, d, p, L, ys, acc);
-        else sum_rows<TY, K, A>(p, L, ys, acc);
-        A* ha = hub_acc + (size_t)h * Sp + lane * K;
+        for (int k = 0; k < KG; ++k) acc[k] = (A)0;
+        if constexpr (kBulk) ring_sum_list<TY, KG, A>(rg, d, p, L, ysg, acc, pol, cold, hot_n);
+        else sum_rows<TY, KG, A>(p, L, ysl, G, acc, -1, pol, cold, hot_n, act != 0);
+        A* ha = hub_acc + (size_t)h * Sp + c0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) atomicAdd(ha + k, acc[k]);
+        for (int k = 0; k < KG; ++k) atomicAdd(ha + k, acc[k]);
         __threadfence();
         int last = 0;
         if (lane == 0) {
           const int np = (full + hub_piece - 1) / hub_piece;
-          last = atomicAdd(&d.hub_cnt[h], 1) == np - 1;
+          last = atomicAdd(&M.hub_cnt[h * 8 + g], 1) == np - 1;
         }
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last) {
           __threadfence();
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
+          for (int k = 0; k < KG; ++k) {
             acc[k] = __ldcg(ha + k);
             ha[k] = (A)0;
           }
-          if (lane == 0) d.hub_cnt[h] = 0;
-          alignas(16) double rr[K];
-          load_cg(M.r + (size_t)v * Sp + lane * K, rr);
-          finish_row<TY, K, A>(d, v, acc, scale_of<A>(d, v), rr, act, yd, l1);
+          if (lane == 0) M.hub_cnt[h * 8 + g] = 0;
+          const A s = scale_of<A>(d, v);
+          alignas(16) double rr[KG];
+          alignas(16) TY eo[KG];
+#pragma unroll
+          for (int k = 0; k < KG; ++k) eo[k] = from_acc((A)0, (TY*)nullptr);
+          if (act) {
+            ld_pol(M.r + rbase_of(v), rr, pol.once);
+            if (FB && s != (A)0) ld_pol(eb + ybase_of(v), eo, pol.once);
+          }
+          finish_slice<TY, KG, A>(M, rbase_of(v), ybase_of(v), acc, s, true, rr, eo, act, yd, l1, pol);
         }
         continue;
       }
-      const int task = t - n_pieces;
-      const int c0 = __ldg(d.task_first + task), c1 = __ldg(d.task_first + task + 1);
-      for (int vb = c0; vb < c1; vb += 32) {
-        // offsets and lengths of up to 32 consecutive nodes in one coalesced load
+      const int task = ti - n_pieces;
+      const int c0t = __ldg(d.task_first + task), c1t = __ldg(d.task_first + task + 1);
+      for (int vb = c0t; vb < c1t; vb += 32) {
+        // offsets, lengths and scales of up to 32 consecutive nodes, coalesced
         const int vl = vb + lane;
         int my_len = 0;
         unsigned my_off = 0;
-        if (vl < c1) {
+        A my_s = (A)0;
+        if (vl < c1t) {
           my_len = __ldg(d.len_c + vl);
           my_off = __ldg(d.off_c + vl);
+          my_s = scale_of<A>(d, vl);
         }
-        const int cnt = min(32, c1 - vb);
-        // empty in-lists: x(i)[v] = 0, R unchanged, the next gather row is zero
-        unsigned empty = __ballot_sync(0xffffffffu, lane < cnt && my_len == 0);
-        while (empty) {
-          const int jj = __ffs(empty) - 1;
-          empty &= empty - 1;
-          alignas(16) TY z[K];
-#pragma unroll
-          for (int k = 0; k < K; ++k) z[k] = from_acc((A)0, (TY*)nullptr);
-          store_k(yd + (size_t)(vb + jj) * Sp + lane * K, z);
-        }
-        // the others (hubs excepted) in order, two deep: the first 32 in-list ids
-        // and the row of R of the next node load while the current one is summed
-        unsigned todo = __ballot_sync(0xffffffffu, lane < cnt && my_len > 0 && my_len <= hub_thr);
+        const int cnt = min(32, c1t - vb);
+        // a node with an in-list adds x(i) into R; a node with out-edges writes
+        // its next gather row (zero, or the carried residual, without in-list)
+        unsigned todo = __ballot_sync(0xffffffffu, lane < cnt && my_len <= hub_thr &&
+                                                       (my_len > 0 || my_s != (A)0));
         if (!todo) continue;
         if constexpr (kBulk) {
           // batches of up to kRows rows of one in-list, nodes in order: the next
           // batch's copies and the ids of the one after are in flight while a
           // batch is summed; a node's row of R loads with its first batch
-          constexpr int G = RingCfg<TY, K>::kRows;
+          constexpr int GR = RingCfg<TY, KG>::kRows;
           int pj = 0, plen = 0, ps = 0;
           unsigned poff = 0;
+          // nodes without in-list: their gather row only
+          unsigned empty = todo & __ballot_sync(0xffffffffu, my_len == 0);
+          todo &= ~empty;
+          while (empty) {
+            const int jj = __ffs(empty) - 1;
+            empty &= empty - 1;
+            const int v = vb + jj;
+            const A s = __shfl_sync(0xffffffffu, my_s, jj);
+            A acc[KG];
+            alignas(16) double rr[KG];
+            alignas(16) TY eo[KG];
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+              acc[k] = (A)0;
+              rr[k] = 0.0;
+              eo[k] = from_acc((A)0, (TY*)nullptr);
+            }
+            if (FB && act) ld_pol(eb + ybase_of(v), eo, pol.once);
+            finish_slice<TY, KG, A>(M, rbase_of(v), ybase_of(v), acc, s, false, rr, eo, act, yd, l1, pol);
+          }
+          if (!todo) continue;
           auto next = [&](RowBatch& o) -> bool {
             if (ps >= plen) {
               if (!todo) return false;
@@ -746,10 +1041,10 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
             o.jc = pj;
             o.off = poff;
             o.s = ps;
-            o.cnt = min(G, plen - ps);
+            o.cnt = min(GR, plen - ps);
             o.first = ps == 0;
-            o.last = ps + G >= plen;
-            ps += G;
+            o.last = ps + GR >= plen;
+            ps += GR;
             return true;
           };
           auto ids_of = [&](const RowBatch& o) -> int {
@@ -758,45 +1053,56 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
               u = 0;
             return u;
           };
-          RowBatch c0, c1, c2;
-          next(c0);
-          ring_issue<TY, K>(rg, rg.buf, c0.cnt, ids_of(c0), ys);
-          alignas(16) double rr_n[K];
-          load_cg(M.r + (size_t)(vb + c0.jc) * Sp + lane * K, rr_n);
-          A s_n = scale_of<A>(d, vb + c0.jc);
-          bool h1 = next(c1);
-          int u1 = h1 ? ids_of(c1) : 0;
-          alignas(16) double rr[K];
+          RowBatch b0, b1, b2;
+          next(b0);
+          ring_issue<TY, KG>(rg, rg.buf, b0.cnt, ids_of(b0), ysg, pol, cold, hot_n);
+          alignas(16) double rr_n[KG];
+          alignas(16) TY eo_n[KG];
+#pragma unroll
+          for (int k = 0; k < KG; ++k) rr_n[k] = 0.0;
+          if (act) ld_pol(M.r + rbase_of(vb + b0.jc), rr_n, pol.once);
+          A s_n = __shfl_sync(0xffffffffu, my_s, b0.jc);
+#pragma unroll
+          for (int k = 0; k < KG; ++k) eo_n[k] = from_acc((A)0, (TY*)nullptr);
+          if (FB && act && s_n != (A)0) ld_pol(eb + ybase_of(vb + b0.jc), eo_n, pol.once);
+          bool h1 = next(b1);
+          int u1 = h1 ? ids_of(b1) : 0;
+          alignas(16) double rr[KG];
+          alignas(16) TY eo[KG];
           A s = (A)0;
-          A acc[K];
+          A acc[KG];
 #pragma unroll
-          for (int k = 0; k < K; ++k) acc[k] = (A)0;
+          for (int k = 0; k < KG; ++k) acc[k] = (A)0;
           for (;;) {
-            if (c0.first) {
+            if (b0.first) {
 #pragma unroll
-              for (int k = 0; k < K; ++k) {
+              for (int k = 0; k < KG; ++k) {
                 rr[k] = rr_n[k];
+                eo[k] = eo_n[k];
                 acc[k] = (A)0;
               }
               s = s_n;
             }
             const int b = rg.buf;
             if (h1) {
-              ring_issue<TY, K>(rg, b ^ 1, c1.cnt, u1, ys);
-              if (c1.first) {
-                load_cg(M.r + (size_t)(vb + c1.jc) * Sp + lane * K, rr_n);
-                s_n = scale_of<A>(d, vb + c1.jc);
+              ring_issue<TY, KG>(rg, b ^ 1, b1.cnt, u1, ysg, pol, cold, hot_n);
+              if (b1.first) {
+                if (act) ld_pol(M.r + rbase_of(vb + b1.jc), rr_n, pol.once);
+                s_n = __shfl_sync(0xffffffffu, my_s, b1.jc);
+                if (FB && act && s_n != (A)0) ld_pol(eb + ybase_of(vb + b1.jc), eo_n, pol.once);
               }
             }
-            const bool h2 = h1 && next(c2);
-            const int u2 = h2 ? ids_of(c2) : 0;
+            const bool h2 = h1 && next(b2);
+            const int u2 = h2 ? ids_of(b2) : 0;
             ring_wait(rg, b, ctl);
-            ring_sum<TY, K, A>(rg, b, c0.cnt, acc);
-            if (c0.last) finish_row<TY, K, A>(d, vb + c0.jc, acc, s, rr, act, yd, l1);
+            ring_sum<TY, KG, A>(rg, b, b0.cnt, acc);
+            if (b0.last)
+              finish_slice<TY, KG, A>(M, rbase_of(vb + b0.jc), ybase_of(vb + b0.jc), acc, s, true,
+                                      rr, eo, act, yd, l1, pol);
             if (!h1) break;
             rg.buf = b ^ 1;
-            c0 = c1;
-            c1 = c2;
+            b0 = b1;
+            b1 = b2;
             h1 = h2;
             u1 = u2;
           }
@@ -806,38 +1112,54 @@ __global__ void __launch_bounds__(kPropThreads, 2) k_propagate_multi(Dev d, Prop
         todo &= todo - 1;
         int len_n = __shfl_sync(0xffffffffu, my_len, jn);
         unsigned off_n = __shfl_sync(0xffffffffu, my_off, jn);
+        A s_n = __shfl_sync(0xffffffffu, my_s, jn);
         int idx_n = lane < len_n ? __ldg(d.pool_c + off_n + lane) : 0;
-        alignas(16) double rr_n[K];
-        load_cg(M.r + (size_t)(vb + jn) * Sp + lane * K, rr_n);
+        alignas(16) double rr_n[KG];
+        alignas(16) TY eo_n[KG];
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          rr_n[k] = 0.0;
+          eo_n[k] = from_acc((A)0, (TY*)nullptr);
+        }
+        if (act && len_n > 0) ld_pol(M.r + rbase_of(vb + jn), rr_n, pol.once);
+        if (FB && act && s_n != (A)0) ld_pol(eb + ybase_of(vb + jn), eo_n, pol.once);
         for (;;) {
           const int jc = jn, len = len_n;
           const unsigned off = off_n;
           const int idx = idx_n;
-          alignas(16) double rr[K];
+          const A s = s_n;
+          alignas(16) double rr[KG];
+          alignas(16) TY eo[KG];
 #pragma unroll
-          for (int k = 0; k < K; ++k) rr[k] = rr_n[k];
+          for (int k = 0; k < KG; ++k) {
+            rr[k] = rr_n[k];
+            eo[k] = eo_n[k];
+          }
           const bool more = todo != 0;
           if (more) {
             jn = __ffs(todo) - 1;
             todo &= todo - 1;
             len_n = __shfl_sync(0xffffffffu, my_len, jn);
             off_n = __shfl_sync(0xffffffffu, my_off, jn);
+            s_n = __shfl_sync(0xffffffffu, my_s, jn);
             idx_n = lane < len_n ? __ldg(d.pool_c + off_n + lane) : 0;
-            load_cg(M.r + (size_t)(vb + jn) * Sp + lane * K, rr_n);
+            if (act && len_n > 0) ld_pol(M.r + rbase_of(vb + jn), rr_n, pol.once);
+            if (FB && act && s_n != (A)0) ld_pol(eb + ybase_of(vb + jn), eo_n, pol.once);
           }
           const int v = vb + jc;
-          const A s = scale_of<A>(d, v);
-          A acc[K];
+          A acc[KG];
 #pragma unroll
-          for (int k = 0; k < K; ++k) acc[k] = (A)0;
-          sum_rows<TY, K, A>(d.pool_c + off, len, ys, acc, idx);
-          finish_row<TY, K, A>(d, v, acc, s, rr, act, yd, l1);
+          for (int k = 0; k < KG; ++k) acc[k] = (A)0;
+          if (len > 0)
+            sum_rows<TY, KG, A>(d.pool_c + off, len, ysl, G, acc, idx, pol, cold, hot_n, act != 0);
+          finish_slice<TY, KG, A>(M, rbase_of(v), ybase_of(v), acc, s, len > 0, rr, eo, act, yd, l1, pol);
           if (!more) break;
         }
       }
     }
-    column_partials<K>(M, l1, s_part);
-    if (bar_arrive(ctl, sh)) decide_multi<K>(d, pp, it, m);
+    flush();
+    column_sums();
+    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, it, m);
     if (!bar_release(ctl, sh)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->epoch = epoch + 1;
@@ -850,15 +1172,15 @@ struct MultiFn {
   int smem;  // dynamic shared memory bytes
 };
 
-template <typename TY, int K>
+template <typename TY, int KG>
 MultiFn multi_fn_k(bool bulk) {
-  if (bulk) return {(const void*)k_propagate_multi<TY, K, true>, RingCfg<TY, K>::kSmem};
-  return {(const void*)k_propagate_multi<TY, K, false>, 0};
+  if (bulk) return {(const void*)k_propagate_multi<TY, KG, true>, RingCfg<TY, KG>::kSmem};
+  return {(const void*)k_propagate_multi<TY, KG, false>, 0};
 }
 
 template <typename TY>
-MultiFn multi_fn(int K, bool bulk) {
-  switch (K) {
+MultiFn multi_fn(int KG, bool bulk) {
+  switch (KG) {
     case 1: return multi_fn_k<TY, 1>(bulk);
     case 2: return multi_fn_k<TY, 2>(bulk);
     case 4: return multi_fn_k<TY, 4>(bulk);
@@ -866,16 +1188,16 @@ MultiFn multi_fn(int K, bool bulk) {
   }
 }
 
-MultiFn pick_multi(int precision, int K, bool bulk) {
-  if (precision == OSP_PREC_FP64) return multi_fn<double>(K, bulk);
-  if (precision == OSP_PREC_FP32_ACC64) return multi_fn<float>(K, bulk);
-  return multi_fn<__nv_bfloat16>(K, bulk);
+MultiFn pick_multi(int precision, int KG, bool bulk) {
+  if (precision == OSP_PREC_FP64) return multi_fn<double>(KG, bulk);
+  if (precision == OSP_PREC_FP32_ACC64) return multi_fn<float>(KG, bulk);
+  return multi_fn<__nv_bfloat16>(KG, bulk);
 }
 
 }  // namespace
 
-int propagate_multi_grid(int precision, int K, int num_sms, bool bulk) {
-  const MultiFn f = pick_multi(precision, K, bulk);
+int propagate_multi_grid(int precision, int KG, int num_sms, bool bulk) {
+  const MultiFn f = pick_multi(precision, KG, bulk);
   if (f.smem > 0 &&
       cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem) != cudaSuccess)
     return 0;
@@ -888,12 +1210,12 @@ int propagate_multi_grid(int precision, int K, int num_sms, bool bulk) {
   return g > kMaxGrid ? kMaxGrid : g;
 }
 
-cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int grid,
-                                   bool bulk, cudaStream_t s) {
+cudaError_t launch_propagate_multi(const Dev& d, const PropParams& pp, int precision, int KG,
+                                   int grid, bool bulk, cudaStream_t s) {
   Dev dd = d;
   PropParams p = pp;
   void* args[] = {&dd, &p};
-  const MultiFn f = pick_multi(precision, d.mu.K, bulk);
+  const MultiFn f = pick_multi(precision, KG, bulk);
   return cudaLaunchCooperativeKernel(f.fn, dim3(grid), dim3(kPropThreads), args, (size_t)f.smem, s);
 }
 

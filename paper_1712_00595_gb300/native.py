@@ -33,7 +33,8 @@ EXPORTED = [
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
     "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
     "osp_set_seed_iterations", "osp_get_schedule", "osp_query_slots", "osp_topk_async",
-    "osp_topk_wait", "osp_selftest_wait",
+    "osp_topk_wait", "osp_selftest_wait", "osp_num_nodes", "osp_get_residual_bounds",
+    "osp_device_bytes",
 ]
 
 
@@ -41,7 +42,9 @@ class osp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("max_nodes", C.c_int64), ("push_alpha", C.c_double), ("push_beta", C.c_double),
                 ("max_iter", C.c_int32), ("node_order", C.c_int32), ("use_graphs", C.c_int32),
-                ("autotune", C.c_int32), ("seed_gather", C.c_int32)]
+                ("autotune", C.c_int32), ("seed_gather", C.c_int32),
+                ("seed_group", C.c_int32), ("deterministic", C.c_int32),
+                ("l2_hot_bytes", C.c_int64), ("hbm_budget_bytes", C.c_int64)]
 
 
 class osp_batch_stats(C.Structure):
@@ -53,7 +56,8 @@ class osp_batch_stats(C.Structure):
                 ("push_frontier", C.c_int64), ("push_reached", C.c_int64),
                 ("ms_update", C.c_float), ("ms_propagate", C.c_float),
                 ("kernel_launches", C.c_int32), ("reserved", C.c_int32),
-                ("pull_dst_nodes", C.c_int64), ("pull_src_nodes", C.c_int64)]
+                ("pull_dst_nodes", C.c_int64), ("pull_src_nodes", C.c_int64),
+                ("residual_bound", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +111,9 @@ def load_library(path: str = LIB_PATH):
             "osp_topk_async": (C.c_int, [P, i32, i32, i32, C.c_int]),
             "osp_topk_wait": (C.c_int, [P, i32, P, P, P]),
             "osp_selftest_wait": (C.c_int, [i32, i32, i32]),
+            "osp_num_nodes": (i64, [P]),
+            "osp_get_residual_bounds": (C.c_int, [P, P, i32, P]),
+            "osp_device_bytes": (i64, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -159,7 +166,8 @@ class Engine:
 
     def __init__(self, precision=OSP_PREC_FP32_ACC64, device=0, stream=None, max_nodes=0,
                  push_alpha=0.0, push_beta=0.0, max_iter=0, node_order=0, use_graphs=False,
-                 autotune=False, seed_gather=0):
+                 autotune=False, seed_gather=0, seed_group=0, deterministic=False,
+                 l2_hot_bytes=0, hbm_budget_bytes=0):
         L = load_library()
         opt = osp_options()
         L.osp_default_options(C.byref(opt))
@@ -174,6 +182,10 @@ class Engine:
         opt.use_graphs = int(bool(use_graphs))
         opt.autotune = int(bool(autotune))
         opt.seed_gather = int(seed_gather)
+        opt.seed_group = int(seed_group)
+        opt.deterministic = int(bool(deterministic))
+        opt.l2_hot_bytes = int(l2_hot_bytes)
+        opt.hbm_budget_bytes = int(hbm_budget_bytes)
         h = C.c_void_p()
         s = L.osp_create(C.byref(h), C.byref(opt))
         if s != OSP_OK:
@@ -310,6 +322,19 @@ class Engine:
                                                C.byref(cnt)))
         k = cnt.value
         return it[:k], q[:k], last[:k]
+
+    def num_nodes(self):
+        return int(self._L.osp_num_nodes(self._h))
+
+    def device_bytes(self):
+        return int(self._L.osp_device_bytes(self._h))
+
+    def get_residual_bounds(self, cap=256):
+        """Per seed: the bound on ||rho||_1 of the stored scores (see osp_batch_stats)."""
+        out = np.empty(cap, np.float64)
+        cnt = C.c_int32(0)
+        self._check(self._L.osp_get_residual_bounds(self._h, _ptr(out), int(cap), C.byref(cnt)))
+        return out[: cnt.value]
 
     def get_step_times(self, cap=4096):
         """Microseconds of the x(0) pass and of each propagation step of the last call."""

@@ -78,3 +78,7 @@ def test_host_side_argument_checks(lib):
     opt.seed_gather = 0
     opt.precision = 9
     assert lib.osp_create(C.byref(h), C.byref(opt)) == N.OSP_EINVAL
+    opt.precision = N.OSP_PREC_FP32_ACC64
+    opt.seed_group = 48  # not a multiple of 32 columns
+    assert lib.osp_create(C.byref(h), C.byref(opt)) == N.OSP_EINVAL
+    assert lib.osp_num_nodes(None) == -1 and lib.osp_device_bytes(None) == -1

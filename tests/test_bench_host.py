@@ -19,10 +19,15 @@ def test_alg_bytes_pull_and_push():
 
 
 def test_alg_bytes_seed_block():
+    # two steps; seeds that propagate ran 2 + 1 + 2 steps (col_steps = 5)
     st = {"iterations": 2, "pull_dst_nodes": 30, "pull_src_nodes": 35}
-    m, S = 1000, 64
-    step = 4 * m + 4 * 31 + S * 2 * 35 + S * (2 + 16) * 30 + 8 * S
-    assert bench.multi_alg_bytes(st, m, S, 2) == 2 * step
+    m = 1000
+    fixed = 4 * m + 4 * 31
+    per_col = 2 * 35 + (2 + 16) * 30 + 8
+    assert bench.multi_alg_bytes(st, m, 5, 2) == 2 * fixed + 5 * per_col
+    # every column running every step: the dense count of S columns per step
+    S = 64
+    assert bench.multi_alg_bytes(st, m, 2 * S, 2) == 2 * (fixed + S * per_col)
 
 
 def _free_port():
