@@ -252,8 +252,8 @@ osp_status osp_query_device(osp_ctx *ctx, int32_t seed_idx, int normalize, doubl
 osp_status osp_topk(osp_ctx *ctx, int32_t seed_idx, int32_t k, int normalize, int32_t *ids,
                     double *scores, int32_t *k_out);
 
-/* Largest n accepted by osp_topk_noalloc. */
-#define OSP_TOPK_NOALLOC_MAX_N 16777216
+/* Largest n accepted by osp_topk_noalloc (the engine's node-id limit, 2^25 - 1). */
+#define OSP_TOPK_NOALLOC_MAX_N 33554431
 
 /* Top-k of a score vector that is already on the device, for callers that
  * cannot allocate device memory when they query: a process whose device memory
@@ -265,17 +265,19 @@ osp_status osp_topk(osp_ctx *ctx, int32_t seed_idx, int32_t k, int normalize, in
  * Arguments, all device pointers on the CURRENT device: scores_device holds n
  * doubles (read only), ids_device receives k int32 indices, out_scores_device
  * k doubles and k_out_device one int32, the number written (min(k, n)).
- * normalize != 0 divides the returned scores by the vector's L1 norm
- * (Theorem 5), which leaves the ranking unchanged. The caller owns every
+ * normalize != 0 divides the returned scores by the vector's L1 norm, which
+ * leaves the ranking unchanged. The caller owns every
  * buffer. The call is asynchronous on `stream` (a cudaStream_t; NULL is the
  * default stream): results are ready when the stream reaches that point.
  *
  * Memory: the call allocates nothing. Its scratch is one fixed array of about
- * 145 KB in the library's own device memory, one per device. The first call on
+ * 180 KB in the library's own device memory, one per device. The first call on
  * each device is the set-up: with that device current it looks the array up
  * (under CUDA's default lazy module loading this loads the library module that
  * holds it, which takes device memory once) and sets the sort kernel's
- * shared-memory limit; make that first call before any stream capture begins. Calls that could run at the same time on the GPU (different
+ * shared-memory limit; make that first call before any stream capture begins.
+ * The set-up is kept for the life of the process: a cudaDeviceReset between
+ * calls is not supported (the array's address and the limit would be stale). Calls that could run at the same time on the GPU (different
  * streams, different host threads) share the array and race; order them.
  *
  * Errors: OSP_EINVAL when n < 0, n > OSP_TOPK_NOALLOC_MAX_N, k is outside

@@ -10,7 +10,9 @@
 //
 // The array is shared by every call on a device, so calls whose kernels could
 // overlap on the GPU (two streams, or two host threads) race on it; callers
-// must order them, for example by issuing them on one stream.
+// must order them, for example by issuing them on one stream. The per-device
+// set-up is done once per process; a cudaDeviceReset between calls (which
+// recreates the context and reloads the module) is not supported.
 #include <mutex>
 
 #include "common.cuh"
@@ -32,7 +34,7 @@ constexpr size_t kOffIds = kOffKeys + align256(sizeof(unsigned long long) * (kTo
 constexpr size_t kOffBlkA = kOffIds + align256(sizeof(int) * (kTopkMaxK + kTopkCand));
 constexpr size_t kOffBlkB = kOffBlkA + align256(sizeof(int) * kMaxChunks);
 constexpr size_t kScratchBytes = kOffBlkB + align256(sizeof(int) * kMaxChunks);
-static_assert(kScratchBytes <= 160 * 1024, "scratch larger than stated in osp.h");
+static_assert(kScratchBytes <= 180 * 1024, "scratch larger than stated in osp.h");
 
 static __device__ __align__(256) unsigned char g_topk_scratch[kScratchBytes];
 

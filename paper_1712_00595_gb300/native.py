@@ -23,7 +23,7 @@ OSP_PREC_FP64, OSP_PREC_FP32_ACC64, OSP_PREC_BF16_ACC64 = 0, 1, 2
 SEED_GATHER_REGISTERS, SEED_GATHER_BULK = 1, 2  # osp_options.seed_gather
 UPDATE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("op", "<i4")])
 
-TOPK_NOALLOC_MAX_N = 16777216  # OSP_TOPK_NOALLOC_MAX_N
+TOPK_NOALLOC_MAX_N = 33554431  # OSP_TOPK_NOALLOC_MAX_N
 MAX_APPLY_OPS = 1 << 22        # ops one apply call accepts (in sub-batches of osp_max_batch())
 
 EXPORTED = [

@@ -63,7 +63,7 @@ def test_rejects_sizes_beyond_the_maximum():
         with pytest.raises(N.OspError) as e:
             N.topk_noalloc(fake, n, k, fake, fake, fake)
         assert e.value.status == N.OSP_EINVAL
-        assert "16777216" in str(e.value)
+        assert str(N.TOPK_NOALLOC_MAX_N) in str(e.value)
 
 
 @pytest.mark.gpu
@@ -88,8 +88,10 @@ def test_noalloc_matches_osp_topk_on_consecutive_calls(make):
         want_ids, want_sc = eng.topk(k, normalize=normalize)
         for call in range(2):
             free0 = torch.cuda.mem_get_info(0)[0]
+            allocs0 = torch.cuda.memory_stats(0).get("allocation.all.allocated", 0)
             out.run(r_dev, k, normalize)
             free1 = torch.cuda.mem_get_info(0)[0]
+            allocs1 = torch.cuda.memory_stats(0).get("allocation.all.allocated", 0)
             ids, sc = out.result()
             assert np.array_equal(ids, want_ids), (k, normalize, call)
             if normalize:
@@ -97,7 +99,11 @@ def test_noalloc_matches_osp_topk_on_consecutive_calls(make):
                 assert np.allclose(sc, want_sc, rtol=1e-14, atol=0)
             else:
                 assert np.array_equal(sc, want_sc)
-            # nothing on the device was allocated by the call itself
+            # nothing on the device was allocated by the call itself: no new
+            # allocation in this process (torch's allocator counts), and the
+            # device's free memory unchanged (this assumes no other context is
+            # allocating on the GPU meanwhile)
+            assert allocs1 == allocs0, (k, normalize, call)
             assert free1 == free0, (k, normalize, call)
     eng.close()
 
@@ -117,3 +123,26 @@ def test_noalloc_short_vectors():
     empty = torch.empty(0, dtype=torch.float64, device="cuda:0")
     ids, sc = _noalloc(torch, empty, 5, False)
     assert ids.size == 0 and sc.size == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [N.TOPK_NOALLOC_MAX_N, N.TOPK_NOALLOC_MAX_N - 1])
+def test_noalloc_at_the_size_limit(n):
+    """The largest vectors accepted (the last chunk full or partial): a seeded
+    random vector with planted ties, against a host sort by (score desc, id
+    asc), twice in a row."""
+    torch = pytest.importorskip("torch")
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(n)
+    r = rng.random(n)
+    r[rng.choice(n, 5000, replace=False)] = 0.999999  # ties inside the top k
+    r[n - 3:] = 1.5  # the last ids rank first
+    order = np.lexsort((np.arange(n), -r))
+    r_dev = torch.from_numpy(r).to("cuda:0")
+    out = _Out(torch)
+    for k in (4096, 100):
+        for _ in range(2):
+            out.run(r_dev, k, False)
+            ids, sc = out.result()
+            assert np.array_equal(ids, order[:k].astype(np.int32))
+            assert np.array_equal(sc, r[order[:k]])
