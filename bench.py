@@ -98,6 +98,9 @@ def parse(argv=None):
                         "engine's choice by row size)")
     p.add_argument("--seed-group", type=int, default=0, choices=[0, 32, 64, 128, 256],
                    help="seed-block workloads: columns per column group (0: the engine's default)")
+    p.add_argument("--l2-hot-bytes", type=int, default=0,
+                   help="seed-block workloads: L2 bytes for the rows of high out-degree "
+                        "sources (0: the engine's default, -1: none)")
     p.add_argument("--fp64-seeds", type=int, default=8,
                    help="several-seed workloads: seeds compared with the FP64 replay (0 = skip)")
     p.add_argument("--e2e-batches", type=int, default=8,
@@ -533,7 +536,8 @@ def run_multi(args, rank, world, name=None, steps=None, warmup=None, extras=True
 
     def engine(p, seed_set):
         e = N.Engine(precision=p, device=local, stream=tstream.cuda_stream, seed_gather=gather,
-                     autotune=args.autotune, node_order=1, seed_group=args.seed_group)
+                     autotune=args.autotune, node_order=1, seed_group=args.seed_group,
+                     l2_hot_bytes=args.l2_hot_bytes)
         e.load_graph(n, src, dst)
         e.set_seeds(seed_set, C_RESTART)
         return e

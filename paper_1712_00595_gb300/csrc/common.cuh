@@ -145,6 +145,7 @@ struct Dev {
   unsigned* pc;                       // [nc + 1]  pc[v] = sum of in-list lengths below v
   int* task_first;                    // [(kMultiNodeItems nc + pool cap) / kMinTaskItems + 2] first node of each warp task
   int* hubs; int* hub_pstart; double* hub_acc; int* hub_cnt;  // [pool cap / kHubThreshold + 2]
+  int* piece_hub;  // [2 pool cap / kMultiHub + 4] the long in-list each piece belongs to
   int* big_u; double* big_y;  // push step: rows longer than kHubThreshold [pool cap / kHubThreshold + 2]
   // reductions and history
   double* part_l1; long long* part_ef;  // [kMaxGrid]

@@ -1064,6 +1064,8 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
     const int64_t nh = (int64_t)(cap / kMultiHub) + 2;
     AL(d.hubs, nh, 0);
     AL(d.hub_pstart, nh + 1, 0);
+    // pieces: at most m / piece + (lists) <= 2 cap / kMultiHub, pieces never shorter than kMultiHub
+    AL(d.piece_hub, 2 * nh + 4, 0);
     AL(d.hub_acc, nh, 0);
     AL(d.hub_cnt, nh, 0);
     const int64_t nb = (int64_t)(cap / kHubThreshold) + 2;  // push: rows above kHubThreshold
@@ -1296,7 +1298,9 @@ osp_status autotune(osp_ctx* ctx, double eps) {
     if (s == OSP_OK) s = plan_pull(ctx, ctx->n, ctx->m);
     if (s != OSP_OK) return s;
     CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-    s = enqueue_propagate(ctx, pp, true);
+    // time the kernel the batches will run (bf16 gather rows included; the
+    // scores of these trial steps are discarded)
+    s = enqueue_propagate(ctx, pp, false);
     if (s != OSP_OK) return s;
     CK(cudaEventRecord(ctx->ev[2], ctx->stream));
     CK(cudaEventSynchronize(ctx->ev[2]));

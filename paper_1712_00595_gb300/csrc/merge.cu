@@ -411,7 +411,9 @@ __global__ void __launch_bounds__(1024) k_hub_prefix(Dev d, int hub_piece) {
   int base = (w ? s_w[w - 1] : 0) + x - mine;
   for (int h = lo; h < hi; ++h) {
     d.hub_pstart[h] = base;
-    base += (d.len_c[d.hubs[h]] + hub_piece - 1) / hub_piece;
+    const int np = (d.len_c[d.hubs[h]] + hub_piece - 1) / hub_piece;
+    for (int q = 0; q < np; ++q) d.piece_hub[base + q] = h;  // a piece finds its list in one load
+    base += np;
     d.hub_acc[h] = 0.0;
     d.hub_cnt[h] = 0;
   }

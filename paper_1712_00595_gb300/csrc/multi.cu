@@ -71,6 +71,10 @@ __device__ __forceinline__ void store_k(T* p, const T (&v)[K]) {
   }
 }
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
 // ---------------------------------------------------------------------------
 // L2 eviction priorities. Source rows of the gather block whose internal id is
 // below PropParams::hot_n (with the degree node order: the most-read rows) are
@@ -289,6 +293,195 @@ __device__ __forceinline__ A scale_of(const Dev& d, int v) {
   return std::is_same<A, double>::value ? (A)__ldg(d.scale_d + v) : (A)__ldg(d.scale_f + v);
 }
 
+// ---------------------------------------------------------------------------
+// Team gather for bf16 rows of a 32-column group (64 bytes). The warp works as
+// 4 teams of 8 lanes; lane (team t, sub s) loads columns [4 s, 4 s + 4) of a
+// row (8 bytes), so one load instruction brings 4 rows. A window is 32
+// consecutive positions of an edge stream (the in-lists of a run of nodes, or
+// one piece of a long in-list); team t takes positions 8 t .. 8 t + 7 of it.
+// Ids are loaded two windows ahead and rows one window ahead, so that up to
+// 64 rows per warp are in flight whatever the list lengths.
+// ---------------------------------------------------------------------------
+struct TeamWin {
+  uint2 v[8];  // this lane's 4 columns of its team's 8 rows (bf16 pairs)
+};
+
+__device__ __forceinline__ void team_load(TeamWin& w, int idx, const __nv_bfloat16* ysg, bool on,
+                                          const L2Pol& pol, unsigned long long cold, int hot_n) {
+  const int lane = threadIdx.x & 31;
+  const int base = lane & 24, sub = lane & 7;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int u = __shfl_sync(0xffffffffu, idx, base + k);
+    w.v[k] = make_uint2(0u, 0u);
+    if (on && u >= 0) {
+      const unsigned long long pp = u < hot_n ? pol.keep : cold;
+      asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                   : "=r"(w.v[k].x), "=r"(w.v[k].y)
+                   : "l"(ysg + (size_t)u * 32 + 4 * sub), "l"(pp));
+    }
+  }
+}
+
+// acc (4 columns) += one row slice of 4 bf16 values (the low half of each
+// 32-bit word is the lower column); two packed f32x2 additions.
+__device__ __forceinline__ void team_add(float (&acc)[4], uint2 x) {
+  unsigned long long a01, a23, v01, v23;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a01) : "f"(acc[0]), "f"(acc[1]));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a23) : "f"(acc[2]), "f"(acc[3]));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v01) : "r"(x.x << 16), "r"(x.x & 0xFFFF0000u));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v23) : "r"(x.y << 16), "r"(x.y & 0xFFFF0000u));
+  asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a01) : "l"(v01));
+  asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a23) : "l"(v23));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[0]), "=f"(acc[1]) : "l"(a01));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2]), "=f"(acc[3]) : "l"(a23));
+}
+
+// Sum of the rows of one piece of a long in-list (ids p[0 .. L)). Returns, in
+// the lanes of team 0 (sub s: columns [4 s, 4 s + 4)), the sums over the
+// whole piece; other lanes hold partial sums.
+__device__ __forceinline__ void team_piece(const int* p, int L, const __nv_bfloat16* ysg, bool on,
+                                           const L2Pol& pol, unsigned long long cold, int hot_n,
+                                           float (&acc)[4]) {
+  const int lane = threadIdx.x & 31;
+  const int nwin = (L + 31) >> 5;
+  auto id_of = [&](int i) -> int {
+    const int q = i * 32 + lane;
+    return (i < nwin && q < L) ? __ldg(p + q) : -1;
+  };
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc[c] = 0.f;
+  // ids run four windows ahead of the rows they name, rows one window ahead
+  // of the additions
+  int i0 = id_of(0), i1 = id_of(1), i2 = id_of(2), i3 = id_of(3);
+  TeamWin A, B;
+  team_load(A, i0, ysg, on, pol, cold, hot_n);
+  for (int i = 0; i < nwin; i += 2) {
+    const int i4 = id_of(i + 4);
+    if (i + 1 < nwin) team_load(B, i1, ysg, on, pol, cold, hot_n);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) team_add(acc, A.v[k]);
+    if (i + 1 >= nwin) break;
+    const int i5 = id_of(i + 5);
+    if (i + 2 < nwin) team_load(A, i2, ysg, on, pol, cold, hot_n);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) team_add(acc, B.v[k]);
+    i1 = i3;
+    i2 = i4;
+    i3 = i5;
+  }
+  // the 4 teams' partial sums, combined in a fixed order
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 8);
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+  }
+}
+
+// The in-lists of a run of up to 32 nodes as one edge stream: lane j holds
+// node j's list length ll (0 to leave it out) and pool offset off; the sums
+// per node and column land in acc_s[j * 32 + column] (shared memory of this
+// warp, zeroed by the caller) through shared-memory atomics, one per column
+// and run of a node's rows inside a team.
+__device__ __forceinline__ void team_stream(const int* pool, int ll, unsigned off,
+                                            const __nv_bfloat16* ysg, bool on, const L2Pol& pol,
+                                            unsigned long long cold, int hot_n, float* acc_s) {
+  const int lane = threadIdx.x & 31;
+  const int base = lane & 24, sub = lane & 7;
+  int incl = ll;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int P = incl - ll;
+  const int E = __shfl_sync(0xffffffffu, incl, 31);
+  if (E == 0) return;
+  const int nwin = (E + 31) >> 5;
+  // position q of the stream: node j = the last lane with P_j <= q, id from its list
+  auto at = [&](int i, int& node) -> int {
+    const int q = i * 32 + lane;
+    int j = 0;
+#pragma unroll
+    for (int b = 16; b >= 1; b >>= 1) {
+      const int Pc = __shfl_sync(0xffffffffu, P, j + b);
+      if (Pc <= q) j += b;
+    }
+    const int Pj = __shfl_sync(0xffffffffu, P, j);
+    const unsigned oj = __shfl_sync(0xffffffffu, off, j);
+    node = -1;
+    if (i >= nwin || q >= E) return -1;
+    node = j;
+    return __ldg(pool + oj + (unsigned)(q - Pj));
+  };
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  int cur = -1;
+  // edge: the current node has rows at the first or last row of one of this
+  // team's runs, so other teams or windows may hold rows of it too (its sum
+  // goes in by atomic additions); a node met only inside one run belongs to
+  // this team alone and its sum is stored once
+  bool edge = false;
+  auto flush = [&]() {
+    if (cur >= 0 && on) {
+      float* a = acc_s + cur * 32 + 4 * sub;
+      if (edge) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) atomicAdd(a + c, acc[c]);
+      } else {
+        *reinterpret_cast<float4*>(a) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = 0.f;
+  };
+  auto eat = [&](const TeamWin& w, int nodes) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int jj = __shfl_sync(0xffffffffu, nodes, base + k);
+      if (jj != cur) {
+        flush();
+        cur = jj;
+        edge = k == 0;
+      }
+      team_add(acc, w.v[k]);
+    }
+    edge = true;  // the run's last node may go on in the next team or window
+  };
+  // ids (and nodes) run four windows ahead of the rows they name, rows one
+  // window ahead of the additions
+  int n0, n1, n2, n3, n4, n5;
+  int i0 = at(0, n0), i1 = at(1, n1), i2 = at(2, n2), i3 = at(3, n3);
+  TeamWin A, B;
+  team_load(A, i0, ysg, on, pol, cold, hot_n);
+  for (int i = 0; i < nwin; i += 2) {
+    const int i4 = at(i + 4, n4);
+    if (i + 1 < nwin) team_load(B, i1, ysg, on, pol, cold, hot_n);
+    eat(A, n0);
+    if (i + 1 >= nwin) break;
+    const int i5 = at(i + 5, n5);
+    if (i + 2 < nwin) team_load(A, i2, ysg, on, pol, cold, hot_n);
+    eat(B, n1);
+    n0 = n2;
+    n1 = n3;
+    n2 = n4;
+    n3 = n5;
+    i1 = i3;
+    i2 = i4;
+    i3 = i5;
+  }
+  flush();
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), and the wait for this
+// thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Whole last CTA: per-column sums of the partials (fixed order over CTAs),
 // per-column stopping, the call's stop, the column groups still running and
 // the history entry (max over the columns that ran the step). A column whose
@@ -425,9 +618,6 @@ struct Ring {
   int buf;                      // the buffer the next batch goes to
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
@@ -736,11 +926,18 @@ __global__ void k_gather_col(const double* __restrict__ r, int Sp, int col,
     out[i] = r[(size_t)ext2int[i] * Sp + col];
 }
 
-// CTAs per SM the seed-block kernel is built for: three when a lane's share
-// of a gather row is at most 4 bytes (few registers), else two.
+// CTAs per SM the seed-block kernel is built for: the team gather of bf16
+// 32-column groups is built for OSP_TEAM_OCC (default 3; measured 7.3 ms per
+// group pass at R-MAT 2^24 against 8.8 ms with 2) CTAs; otherwise three when a
+// lane's share of a gather row is at most 4 bytes (few registers), else two.
+#ifndef OSP_TEAM_OCC
+#define OSP_TEAM_OCC 3
+#endif
 template <typename TY, int KG>
 struct MultiOcc {
-  static constexpr int value = KG * (int)sizeof(TY) <= 4 ? 3 : 2;
+  static constexpr int value = std::is_same<TY, __nv_bfloat16>::value && KG == 1
+                                   ? OSP_TEAM_OCC
+                                   : (KG * (int)sizeof(TY) <= 4 ? 3 : 2);
 };
 
 // The seed block, one persistent cooperative launch per call: the x(0) pass
@@ -760,6 +957,11 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   using A = typename AccOf<TY>::type;
   constexpr int G = 32 * KG;
   constexpr bool FB = Feedback<TY>::on;
+  // bf16 rows of 32-column groups are gathered by teams of 8 lanes over a flat
+  // edge stream (team_stream / team_piece); the other forms walk node by node
+  constexpr bool kTeam = std::is_same<TY, __nv_bfloat16>::value && KG == 1 && !kBulk;
+  __shared__ float s_team_acc[kTeam ? kPropWarps * 1024 : 1];                 // node x column sums
+  __shared__ __align__(16) __nv_bfloat16 s_team_e[kTeam ? kPropWarps * 1024 : 8];  // residual rows
   __shared__ BarShared sh;
   __shared__ double s_part[kPropWarps * kMaxSeeds];  // per warp, per column |x| sums
   __shared__ int s_grp[8];
@@ -899,6 +1101,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
     const long long total = (long long)s_ngrp * n_items;
     int cur = -1;  // column group of the items this warp works on now
     unsigned act = 0;
+    bool on4 = false;
     double l1[KG];
 #pragma unroll
     for (int k = 0; k < KG; ++k) l1[k] = 0.0;
@@ -926,6 +1129,11 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
 #pragma unroll
         for (int k = 0; k < KG; ++k)
           act |= (unsigned)(*(volatile int*)&M.active[g * G + lane * KG + k] != 0) << k;
+        if constexpr (kTeam) {
+          // team gathers: lane (t, s) loads columns [4 s, 4 s + 4) of a row
+          const unsigned am = __ballot_sync(0xffffffffu, act != 0);
+          on4 = ((am >> (4 * (lane & 7))) & 0xFu) != 0;
+        }
       }
       const TY* ysg = ys + g * gs;           // the group's gather rows, G elements apart
       const TY* ysl = ysg + lane * KG;       // this lane's columns of them
@@ -934,18 +1142,47 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       auto ybase_of = [&](int v) { return g * gs + (size_t)v * G + lane * KG; };
       if (ti < n_pieces) {
         // a piece of a long in-list; the piece that completes the list finishes it
-        int lo = 0, hi = n_hubs;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (__ldg(d.hub_pstart + mid) <= ti) lo = mid;
-          else hi = mid;
-        }
-        const int h = lo;
+        const int h = __ldg(d.piece_hub + ti);
         const int v = __ldg(d.hubs + h);
         const int piece = ti - __ldg(d.hub_pstart + h);
         const int full = __ldg(d.len_c + v);
         const int* p = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * hub_piece);
         const int L = min(hub_piece, full - piece * hub_piece);
+        if constexpr (kTeam) {
+          float a4[4];
+          team_piece(p, L, ysg, on4, pol, cold, hot_n, a4);
+          float* ha4 = (float*)hub_acc + (size_t)h * Sp + (size_t)g * G + 4 * lane;
+          if (lane < 8 && on4) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(ha4 + c, a4[c]);
+          }
+          __threadfence();
+          int last = 0;
+          if (lane == 0) {
+            const int np = (full + hub_piece - 1) / hub_piece;
+            last = atomicAdd(&M.hub_cnt[h * 8 + g], 1) == np - 1;
+          }
+          last = __shfl_sync(0xffffffffu, last, 0);
+          if (last) {
+            __threadfence();
+            float* hx = (float*)hub_acc + (size_t)h * Sp + c0;  // lane = column
+            const float x = __ldcg(hx);
+            *hx = 0.f;
+            if (lane == 0) M.hub_cnt[h * 8 + g] = 0;
+            const float sv = scale_of<float>(d, v);
+            if (act) {
+              atomicAdd(M.r + rbase_of(v), (double)x);
+              l1[0] += fabs((double)x);
+              if (sv != 0.f) {
+                const float w = x * sv + __bfloat162float(eb[ybase_of(v)]);
+                const __nv_bfloat16 yv = __float2bfloat16_rn(w);
+                yd[ybase_of(v)] = yv;
+                eb[ybase_of(v)] = __float2bfloat16_rn(w - __bfloat162float(yv));
+              }
+            }
+          }
+          continue;
+        }
         A acc[KG];
 #pragma unroll
         for (int k = 0; k < KG; ++k) acc[k] = (A)0;
@@ -984,6 +1221,72 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       }
       const int task = ti - n_pieces;
       const int c0t = __ldg(d.task_first + task), c1t = __ldg(d.task_first + task + 1);
+      if constexpr (kTeam) {
+        float* acc_s = s_team_acc + wid * 1024;
+        __nv_bfloat16* e_s = s_team_e + wid * 1024;
+        // list lengths, offsets and scales of the next run of 32 nodes load
+        // while the current run is summed
+        int nx_len = 0;
+        unsigned nx_off = 0;
+        float nx_s = 0.f;
+        auto header = [&](int vb) {
+          const int vl = vb + lane;
+          nx_len = 0;
+          nx_off = 0;
+          nx_s = 0.f;
+          if (vl < c1t) {
+            nx_len = __ldg(d.len_c + vl);
+            nx_off = __ldg(d.off_c + vl);
+            nx_s = scale_of<float>(d, vl);
+          }
+        };
+        header(c0t);
+        for (int vb = c0t; vb < c1t; vb += 32) {
+          const int vl = vb + lane;
+          const int my_len = nx_len;
+          const unsigned my_off = nx_off;
+          const float my_s = nx_s;
+          if (vb + 32 < c1t) header(vb + 32);
+          const bool mine = vl < c1t && my_len <= hub_thr;  // hubs go by pieces
+          const unsigned fin = __ballot_sync(0xffffffffu, mine && (my_len > 0 || my_s != 0.f));
+          if (!fin) continue;
+          // this node's residual row (all 32 columns) into shared memory, in flight
+          // while the stream runs
+          if (((fin >> lane) & 1u) && my_s != 0.f) {
+            const __nv_bfloat16* er = eb + g * gs + (size_t)vl * G;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp_async16(e_s + lane * 32 + 8 * q, er + 8 * q);
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            reinterpret_cast<float4*>(acc_s)[lane + 32 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          __syncwarp();
+          team_stream(d.pool_c, mine ? my_len : 0, my_off, ysg, on4, pol, cold, hot_n, acc_s);
+          cp_async_wait_all();
+          __syncwarp();
+          // finish: lane = column
+          for (unsigned fb = fin; fb; fb &= fb - 1) {
+            const int j = __ffs(fb) - 1;
+            const int v = vb + j;
+            const float sj = __shfl_sync(0xffffffffu, my_s, j);
+            const bool has_in = __shfl_sync(0xffffffffu, my_len, j) > 0;
+            if (!act) continue;
+            const float x = acc_s[j * 32 + lane];
+            if (has_in) {
+              atomicAdd(M.r + rbase_of(v), (double)x);
+              l1[0] += fabs((double)x);
+            }
+            if (sj != 0.f) {
+              const float w = x * sj + __bfloat162float(e_s[j * 32 + lane]);
+              const __nv_bfloat16 yv = __float2bfloat16_rn(w);
+              yd[ybase_of(v)] = yv;
+              eb[ybase_of(v)] = __float2bfloat16_rn(w - __bfloat162float(yv));
+            }
+          }
+          __syncwarp();
+        }
+        continue;
+      }
       for (int vb = c0t; vb < c1t; vb += 32) {
         // offsets, lengths and scales of up to 32 consecutive nodes, coalesced
         const int vl = vb + lane;

@@ -271,13 +271,7 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= n_items) break;
     if (t < n_pieces) {
-      int lo = 0, hi = n_hubs;  // largest h with hub_pstart[h] <= t
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(d.hub_pstart + mid) <= t) lo = mid;
-        else hi = mid;
-      }
-      const int h = lo;
+      const int h = __ldg(d.piece_hub + t);  // the long list this piece belongs to
       const int v = __ldg(d.hubs + h);
       const int piece = t - __ldg(d.hub_pstart + h);
       const int full = __ldg(d.len_c + v);
