@@ -129,9 +129,15 @@ typedef struct {
                             once per group that still has a running column, so groups whose
                             seeds have all stopped cost nothing; inside a group, a lane whose
                             columns have all stopped loads and stores nothing. */
-    int32_t deterministic; /* != 0: every propagation step pulls (no push steps) and long
-                              in-lists combine their pieces in a fixed order, so one input
-                              gives the same bits on every run (the one-seed path). */
+    int32_t deterministic; /* != 0 (one seed; osp_set_seeds with two or more returns
+                              OSP_ENOTSUP): every propagation step pulls (no push steps, so
+                              each costs a pass over all edges), warps take their work in a
+                              fixed order, long in-lists add their pieces in piece order, and
+                              the batch offset q_offset is summed exactly in fixed point
+                              (units of 2^-62, |error| <= 2^-63 per term). The same calls on
+                              the same device and options then give the same bits in the
+                              scores, the per-step norms and the statistics on every run.
+                              autotune is ignored (a timed choice would change the bits). */
     int64_t l2_hot_bytes; /* seed block with node_order 1: bytes of L2 given to the gather rows
                              of the highest out-degree nodes (kept in L2 before other lines);
                              0 = 60% of the device's L2, < 0 = none. */
@@ -238,7 +244,8 @@ int64_t osp_max_batch(void);
 
 /* Copy the scores of seed seed_idx to out[0 .. n) (host). normalize != 0 returns
  * r / ||r||_1, the dead-end handled vector of Theorem 5 (Sec. 3.4.2); 0 returns
- * the stored, unnormalised r_temp. A deleted node keeps its entry; its exact
+ * the stored, unnormalised r_temp (||r||_1 is summed in a fixed order, so the
+ * same r always gives the same bits). A deleted node keeps its entry; its exact
  * RWR value is 0 and the stored value approaches it like any other entry. */
 osp_status osp_query(osp_ctx *ctx, int32_t seed_idx, int normalize, double *out);
 

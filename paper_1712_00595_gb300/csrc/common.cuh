@@ -23,6 +23,7 @@ constexpr int kNoPos = 0x7F7F7F7F;       // del_pos of a node not deleted by the
 constexpr int kLight = 32;               // lists up to this length are walked by one lane
 constexpr int kPiece = 256;              // old entries per warp task in the list merge
 constexpr int kMaxHist = 4096;           // per-step ||x||_1 history entries
+constexpr int kAbsParts = 1024;  // CTAs of the L1-norm reduction (per-CTA partials, summed in order)
 constexpr int kMaxGrid = 4096;           // CTAs of the persistent kernel (partials array size)
 constexpr int kPropThreads = 256;
 constexpr int kPropWarps = kPropThreads / 32;
@@ -119,6 +120,7 @@ struct Dev {
   double* r;
   void* y0; void* y1;  // gather vectors y = (1-c) x / d (float or double)
   double* xacc;        // push / offset accumulator
+  unsigned long long* xfix;  // deterministic mode: offset accumulator in fixed point (x 2^62), else null
   double* scale_d;     // (1-c) / d_u, 0 for dead-ends
   float* scale_f;
   int* mark;           // frontier membership stamps
@@ -146,6 +148,8 @@ struct Dev {
   int* task_first;                    // [(kMultiNodeItems nc + pool cap) / kMinTaskItems + 2] first node of each warp task
   int* hubs; int* hub_pstart; double* hub_acc; int* hub_cnt;  // [pool cap / kHubThreshold + 2]
   int* piece_hub;  // [2 pool cap / kMultiHub + 4] the long in-list each piece belongs to
+  double* piece_part;  // [as piece_hub] deterministic mode: per-piece partial sums
+  double* hub_l1;      // [as hubs] deterministic mode: |x_v| of each long in-list's node
   int* big_u; double* big_y;  // push step: rows longer than kHubThreshold [pool cap / kHubThreshold + 2]
   // reductions and history
   double* part_l1; long long* part_ef;  // [kMaxGrid]
@@ -176,6 +180,7 @@ struct PropParams {
   double beta;
   int fp32;
   int hot_n;  // seed block: gather rows of internal ids below hot_n are kept in L2 first
+  int det;    // one seed: pull steps only, static work order, long lists combined in order
 };
 
 // ---------------------------------------------------------------------------

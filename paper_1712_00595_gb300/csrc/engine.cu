@@ -473,11 +473,14 @@ osp_status plan_pull(osp_ctx* ctx, int64_t n_bound, int64_t m_bound) {
   const int* sc = schedule(ctx);
   k_pull_plan<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d, sc[1], sc[3], sc[0]);
   ++ctx->launches;
-  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d, sc[2]);
+  k_hub_prefix<<<1, 1024, 0, st>>>(ctx->d, sc[2], ctx->opt.deterministic != 0);
   ++ctx->launches;
   CK(cudaGetLastError());
   return OSP_OK;
 }
+
+// CTAs of the L1-norm reduction: two per SM, at most kAbsParts partials.
+int abs_grid(const osp_ctx* ctx) { return std::min(ctx->num_sms * 2, kAbsParts); }
 
 PropParams prop_params(osp_ctx* ctx, double eps) {
   PropParams pp;
@@ -491,6 +494,7 @@ PropParams prop_params(osp_ctx* ctx, double eps) {
   pp.beta = ctx->opt.push_beta > 0 ? ctx->opt.push_beta : kPushBeta;
   pp.fp32 = ctx->opt.precision == OSP_PREC_FP32_ACC64;
   pp.hot_n = 0;
+  pp.det = ctx->opt.deterministic != 0;
   return pp;
 }
 
@@ -777,8 +781,7 @@ osp_status enqueue_topk(osp_ctx* ctx, cudaStream_t st, const double* rs, int n, 
   k_topk_emit<<<nb, 1024, 0, st>>>(rs, n, t.st, t.blk_a, t.blk_b, t.keys, t.ids);
   ++ctx->launches;
   if (normalize) {
-    CK(cudaMemsetAsync(t.dsum, 0, sizeof(double), st));
-    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(rs, n, t.dsum);
+    k_abs_sum<<<abs_grid(ctx), 256, 0, st>>>(rs, n, t.dsum, t.dsum + 1);
     ++ctx->launches;
   }
   const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
@@ -1015,6 +1018,7 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   d.y0 = y0;
   d.y1 = y1;
   AL(d.xacc, nc, 0);
+  if (ctx->opt.deterministic) AL(d.xfix, nc, 0);
   AL(d.scale_d, nc, 0);
   AL(d.scale_f, nc, 0);
   AL(d.mark, nc, 0);
@@ -1066,6 +1070,8 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
     AL(d.hub_pstart, nh + 1, 0);
     // pieces: at most m / piece + (lists) <= 2 cap / kMultiHub, pieces never shorter than kMultiHub
     AL(d.piece_hub, 2 * nh + 4, 0);
+    AL(d.piece_part, 2 * nh + 4, 0);
+    AL(d.hub_l1, nh, 0);
     AL(d.hub_acc, nh, 0);
     AL(d.hub_cnt, nh, 0);
     const int64_t nb = (int64_t)(cap / kHubThreshold) + 2;  // push: rows above kHubThreshold
@@ -1078,7 +1084,7 @@ osp_status osp_load_graph(osp_ctx* ctx, int64_t n, int64_t m, const int32_t* src
   AL(d.step_ns, kMaxHist + 1, 0);
   AL(d.ctl, 1, 0);
   AL(ctx->ops_stage, kMaxBatch, 0);
-  AL(ctx->dsum, 1, 0);
+  AL(ctx->dsum, kAbsParts + 2, 0);  // the norm, its per-CTA partials, the CTA count
   AL(ctx->dtmp, nc, 0);
   AL(ctx->scan_off, nc, 0);
   AL(ctx->scan_bsum, nc / 4096 + 2, 0);
@@ -1134,6 +1140,8 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
   }
   if (S == 1 && ctx->opt.precision == OSP_PREC_BF16_ACC64)
     return fail(ctx, OSP_ENOTSUP, "bf16 gather vectors are built for two or more seeds");
+  if (S > 1 && ctx->opt.deterministic)
+    return fail(ctx, OSP_ENOTSUP, "the deterministic mode covers the one-seed path");
   CK(cudaSetDevice(ctx->device));
   std::vector<int32_t> s_int(S, 0);
   for (int i = 0; i < S && !pagerank; ++i) {
@@ -1328,7 +1336,7 @@ osp_status osp_init_scores(osp_ctx* ctx, double eps, osp_batch_stats* stats) {
   if (s != OSP_OK) return s;
   if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
   ctx->launches = 0;
-  if (ctx->opt.autotune) {
+  if (ctx->opt.autotune && !ctx->opt.deterministic) {  // a timed choice would vary the bits
     s = autotune(ctx, eps);
     if (s != OSP_OK) return s;
     ctx->launches = 0;
@@ -1380,8 +1388,7 @@ osp_status scores_in_caller_order(osp_ctx* ctx, int col, int normalize, double* 
   else
     k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dst);
   if (normalize) {
-    CK(cudaMemsetAsync(ctx->dsum, 0, sizeof(double), st));
-    k_abs_sum<<<ctx->num_sms * 2, 256, 0, st>>>(dst, n, ctx->dsum);
+    k_abs_sum<<<abs_grid(ctx), 256, 0, st>>>(dst, n, ctx->dsum, ctx->dsum + 1);
     k_scale_copy<<<ctx->num_sms * 2, 256, 0, st>>>(dst, n, ctx->dsum, dst);
   }
   CK(cudaGetLastError());
@@ -1469,7 +1476,7 @@ osp_status osp_query_slots(osp_ctx* ctx, int32_t nslots) {
     QL(t.out_ids, kTopkMaxK);
     QL(t.out_sc, kTopkMaxK);
     QL(t.out_k, 1);
-    QL(t.dsum, 1);
+    QL(t.dsum, kAbsParts + 2);
 #undef QL
     CK(cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming));
   }

@@ -15,7 +15,7 @@ __global__ void k_merge_plan(Dev d);
 __global__ void k_merge_write(Dev d);
 __global__ void k_merge_finish(Dev d);
 __global__ void k_pull_plan(Dev d, int hub_thr, int node_w, int task_items);
-__global__ void k_hub_prefix(Dev d, int hub_piece);
+__global__ void k_hub_prefix(Dev d, int hub_piece, int det);
 __global__ void k_set_scale(Dev d, int n, double c);
 __global__ void k_scan_local(const int* __restrict__ len, unsigned* out, unsigned* bsum, int n);
 __global__ void k_scan_top(unsigned* bsum, int nb);
@@ -23,7 +23,7 @@ __global__ void k_scan_add(unsigned* out, const unsigned* __restrict__ bsum, int
 __global__ void k_compact_copy(const unsigned* __restrict__ off_old, const int* __restrict__ len,
                                const int* __restrict__ pool_old, const unsigned* __restrict__ off_new,
                                int* pool_new, int n);
-__global__ void k_abs_sum(const double* __restrict__ r, int n, double* out);
+__global__ void k_abs_sum(const double* __restrict__ r, int n, double* out, double* parts);
 __global__ void k_gather_ext(const double* __restrict__ r, const int* __restrict__ ext2int, int n,
                              double* out);
 __global__ void k_scale_copy(const double* r, int n, const double* __restrict__ sum, double* out);

@@ -28,6 +28,13 @@ namespace {
 __device__ __forceinline__ void offset_add(const Dev& d, bool want, int v, double val, int epoch,
                                            bool queue) {
   if (want && !OSP_GUARD(d.ctl, v >= 0 && v < d.nc, "offset target", v, 0, 0)) want = false;
+  if (d.xfix) {
+    // deterministic mode: exact integer sums in units of 2^-62 (|q_offset_v| <=
+    // (1-c) ||r_old||_1 < 2, and two's-complement wrap-around leaves partial
+    // sums harmless), collected by the x(0) scan, so no queue either
+    if (want) atomicAdd(d.xfix + v, (unsigned long long)__double2ll_rn(val * 0x1p62));
+    return;
+  }
   if (want) atomicAdd(&d.xacc[v], val);
   if (!queue) return;
   bool need = want && (d.mark[v] != epoch) && (atomicExch(&d.mark[v], epoch) != epoch);
@@ -382,12 +389,42 @@ __global__ void k_pull_plan(Dev d, int hub_thr, int node_w, int task_items) {
 }
 
 // Pull-step plan, part 2 (one CTA): piece prefix over the long in-lists.
-__global__ void __launch_bounds__(1024) k_hub_prefix(Dev d, int hub_piece) {
+// det != 0: the list of long in-lists, appended in whatever order the warps of
+// k_pull_plan ran, is first rebuilt in ascending node order (one ordered
+// compaction over all nodes), so that the pieces and the per-list norm slots
+// have the same positions on every run.
+__global__ void __launch_bounds__(1024) k_hub_prefix(Dev d, int hub_piece, int det) {
   __shared__ int s_w[32];
+  __shared__ int s_base;
   Ctl* ctl = d.ctl;
   if (*(volatile int*)&ctl->status) return;
-  const int nh = ctl->n_hubs;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (det) {
+    const int n = ctl->n, thr = ctl->hub_thr;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n; b0 += 1024) {
+      const int v = b0 + tid;
+      const bool h = v < n && d.len_c[v] > thr;
+      const unsigned bm = __ballot_sync(0xffffffffu, h);
+      if (lane == 0) s_w[w] = __popc(bm);
+      __syncthreads();
+      if (w == 0) {
+        int x = s_w[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        s_w[lane] = x;
+      }
+      __syncthreads();
+      if (h) d.hubs[s_base + (w ? s_w[w - 1] : 0) + __popc(bm & lanemask_lt())] = v;
+      __syncthreads();
+      if (tid == 0) s_base += s_w[31];
+      __syncthreads();
+    }
+  }
+  const int nh = ctl->n_hubs;
   const int per = (nh + 1023) / 1024;
   const int lo = min(nh, tid * per), hi = min(nh, lo + per);
   int mine = 0;
@@ -526,19 +563,47 @@ __global__ void k_compact_copy(const unsigned* __restrict__ off_old, const int* 
   }
 }
 
-// ||r||_1 (one partial per CTA added atomically) and r / ||r||_1.
-__global__ void k_abs_sum(const double* __restrict__ r, int n, double* out) {
+// ||r||_1 and r / ||r||_1. With parts == nullptr the per-CTA partials are
+// added atomically into *out (cleared by the caller); otherwise each CTA
+// stores its partial in parts[blockIdx.x] and the last CTA to finish adds them
+// in index order into *out, so the norm has the same bits on every run.
+// parts[kAbsParts] (as an unsigned int) counts finished CTAs; the grid must
+// not exceed kAbsParts, and the last CTA resets the count.
+__global__ void k_abs_sum(const double* __restrict__ r, int n, double* out, double* parts) {
   double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     s += fabs(r[i]);
   s = warp_sum(s);
   __shared__ double sw[32];
+  __shared__ bool s_last;
   if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x < 32) {
     double t = threadIdx.x < (blockDim.x >> 5) ? sw[threadIdx.x] : 0.0;
     t = warp_sum(t);
-    if (threadIdx.x == 0) atomicAdd(out, t);
+    if (threadIdx.x == 0) {
+      if (!parts) {
+        atomicAdd(out, t);
+      } else {
+        parts[blockIdx.x] = t;
+        __threadfence();
+        unsigned* cnt = (unsigned*)(parts + kAbsParts);
+        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+      }
+    }
+  }
+  if (!parts) return;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) t += __ldcg(parts + i);
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *(unsigned*)(parts + kAbsParts) = 0u;
+    }
   }
 }
 

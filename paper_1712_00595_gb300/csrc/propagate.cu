@@ -60,6 +60,10 @@ __device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n,
     a += __ldcg(d.part_l1 + i);
     b += __ldcg(d.part_ef + i);
   }
+  if (pp.det && step_mode == kPull) {  // the long in-lists' |x|, in a fixed order too
+    const int nh = ctl->n_hubs;
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) a += __ldcg(d.hub_l1 + i);
+  }
   a = warp_sum(a);
   b = warp_sum(b);
   __syncthreads();
@@ -114,7 +118,7 @@ __device__ void decide(const Dev& d, const PropParams& pp, int step_mode, int n,
     }
   }
   int next = kPull;
-  if (step_mode != kPull) {
+  if (step_mode != kPull && !pp.det) {
     const int qs = *(volatile int*)&ctl->q_size[it & 1];
     const bool dense = (double)EF > (double)m / pp.alpha || (double)qs > (double)n / pp.beta;
     next = dense ? kPull : kPush;
@@ -251,7 +255,8 @@ __device__ __forceinline__ void finish_node(const Dev& d, int v, double x, void*
 // piece that completes a list finishes it).
 template <typename T>
 __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_pieces,
-                            int n_tasks, T* wacc, int* grab, int hub_thr, int hub_piece) {
+                            int n_tasks, T* wacc, int* grab, int hub_thr, int hub_piece,
+                            bool det) {
   constexpr bool kF32 = std::is_same<T, float>::value;
   double l1 = 0.0;
   const int lane = threadIdx.x & 31;
@@ -265,10 +270,18 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
   long long P = 7919;
   if (n_tasks % 7919 == 0) P = 7907;
   if (n_tasks % P == 0) P = 1;
-  for (;;) {
+  // Deterministic mode: warp gw takes items gw, gw + nw, ... instead, so every
+  // lane sums its |x| terms in the same order on every run.
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int k = 0;; ++k) {
     int t = 0;
-    if (lane == 0) t = atomicAdd(grab, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
+    if (det) {
+      t = gw + k * nw;
+    } else {
+      if (lane == 0) t = atomicAdd(grab, 1);
+      t = __shfl_sync(0xffffffffu, t, 0);
+    }
     if (t >= n_items) break;
     if (t < n_pieces) {
       const int h = __ldg(d.piece_hub + t);  // the long list this piece belongs to
@@ -287,15 +300,32 @@ __device__ double pull_step(const Dev& d, const T* ys, T* yd, int n_hubs, int n_
       for (; j < L; j += 32) acc += ys[__ldg(p + j)];
       acc = warp_sum(acc);
       if (lane == 0) {
-        atomicAdd(&d.hub_acc[h], (double)acc);
-        __threadfence();
         const int np = (full + hub_piece - 1) / hub_piece;
-        if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
+        if (det) {
+          // pieces leave their sums in slots; the last one adds them up in
+          // piece order and parks |x_v| for the step's fixed-order norm sum
+          d.piece_part[t] = (double)acc;
           __threadfence();
-          const double x =
-              __longlong_as_double((long long)atomicExch((unsigned long long*)&d.hub_acc[h], 0ull));
-          d.hub_cnt[h] = 0;
-          finish_node(d, v, x, yd, kF32, l1);
+          if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
+            __threadfence();
+            const double* slots = d.piece_part + (t - piece);
+            double x = 0.0;
+            for (int q = 0; q < np; ++q) x += __ldcg(slots + q);
+            d.hub_cnt[h] = 0;
+            double hl = 0.0;
+            finish_node(d, v, x, yd, kF32, hl);
+            d.hub_l1[h] = hl;
+          }
+        } else {
+          atomicAdd(&d.hub_acc[h], (double)acc);
+          __threadfence();
+          if (atomicAdd(&d.hub_cnt[h], 1) == np - 1) {
+            __threadfence();
+            const double x = __longlong_as_double(
+                (long long)atomicExch((unsigned long long*)&d.hub_acc[h], 0ull));
+            d.hub_cnt[h] = 0;
+            finish_node(d, v, x, yd, kF32, l1);
+          }
         }
       }
       continue;
@@ -454,7 +484,26 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
     long long ef = 0;
     const int qs = *(volatile int*)&ctl->q_size[0];
     if (!OSP_GUARD(ctl, qs >= 0 && qs <= d.nc, "first frontier size", qs, 0, 0)) return;
-    if (*(volatile int*)&ctl->dense0) {
+    if (pp.det) {
+      // Deterministic mode: every step pulls, so no frontier queue is kept; a
+      // fixed pass over all nodes collects x(0) from xacc and from the merge's
+      // fixed-point accumulator (exact integer sums, so their order is moot).
+      for (int v = tid; v < n; v += nthreads) {
+        double x = __ldcg(d.xacc + v);
+        const long long q = (long long)__ldcg(d.xfix + v);
+        if (q != 0) {
+          x += (double)q * 0x1p-62;
+          d.xfix[v] = 0ull;
+        }
+        if (x != 0.0) {
+          d.xacc[v] = 0.0;
+          d.r[v] += x;
+          l1 += fabs(x);
+          yb[0][v] = (T)(x * __ldg(d.scale_d + v));
+          ef += __ldg(d.len_r + v);
+        }
+      }
+    } else if (*(volatile int*)&ctl->dense0) {
       // The merge reached more than n/beta nodes and queued none of them: one
       // coalesced pass over all nodes collects x(0) (xacc is zero off its
       // support) and builds the frontier queue of its nonzero entries.
@@ -555,7 +604,8 @@ __global__ void __launch_bounds__(kPropThreads, 4) k_propagate(Dev d, PropParams
       }
     } else {
       l1 = pull_step<T>(d, yb[src], yb[dst], n_hubs, n_pieces, n_tasks,
-                        s_wacc + (threadIdx.x & ~31), &ctl->ctr[1], hub_thr, hub_piece);
+                        s_wacc + (threadIdx.x & ~31), &ctl->ctr[1], hub_thr, hub_piece,
+                        pp.det != 0);
     }
     block_partials(d, l1, ef, s_l1, s_ef);
     if (bar_arrive(ctl, sh)) decide(d, pp, mode, n, m, s_l1, s_ef);

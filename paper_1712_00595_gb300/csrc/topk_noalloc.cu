@@ -117,7 +117,7 @@ extern "C" osp_status osp_topk_noalloc(const double* scores_device, int64_t n, i
   k_topk_emit<<<nb, 1024, 0, st>>>(scores_device, nn, state, blk_a, blk_b, keys, ids);
   if (normalize) {
     if (cudaMemsetAsync(sum, 0, sizeof(double), st) != cudaSuccess) return OSP_ECUDA;
-    k_abs_sum<<<sms * 2, 256, 0, st>>>(scores_device, nn, sum);
+    k_abs_sum<<<sms * 2, 256, 0, st>>>(scores_device, nn, sum, nullptr);
   }
   const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
   k_topk_sort<<<1, 1024, smem, st>>>(scores_device, state, keys, ids, kTopkMaxK + kTopkCand, k,

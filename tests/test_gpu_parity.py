@@ -703,3 +703,67 @@ def test_hbm_budget_option():
     assert ids.size == 10
     assert e.num_nodes() == n
     e.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_deterministic_mode_gives_the_same_bits(prec):
+    """osp_options.deterministic: two contexts fed the same calls (a batch
+    merged in three sub-batches, then mixed batches with node additions and
+    deletions) agree bit for bit in the scores, the normalised scores, the
+    per-step norms and the statistics; every step pulls; autotune is ignored;
+    and the scores still match the oracle at the path's tolerance."""
+    rng = np.random.default_rng(90 + prec)
+    n = 3000
+    src, dst = hub_graph(rng, n=n, m=60000, hub_in=2500, hub_out=900, mids=12)
+    gen = np.random.default_rng(6)
+    sampler = lambda k: (gen.integers(0, n, k), gen.integers(0, n, k))  # noqa: E731
+    big = W.sized_update_stream(src, dst, n, [40000], 4, sampler)[0]
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    assert g.apply(big, protect=(0,)) == -1
+    rp, col = g.csr()
+    src2 = np.repeat(np.arange(rp.size - 1), np.diff(rp)).astype(np.int32)
+    batches = [big] + mixed_sequence(rng, n, src2, col.astype(np.int32), 4, 150)
+    g = O.Graph(n, src, dst)
+    eps = 1e-12
+    runs = []
+    for _ in range(2):
+        eng, st = engine(prec, n, src, dst, eps_init=eps, max_nodes=n + 4096,
+                         deterministic=True, autotune=True)
+        rec = []
+        for ops in [None] + batches:
+            if ops is not None:
+                st = eng.apply_updates(ops, eps)
+            st = {k: v for k, v in st.items() if not k.startswith("ms_")}
+            assert st["push_iterations"] == 0
+            rec.append((st, eng.query(), eng.query(normalize=True), eng.get_l1_history(),
+                        eng.topk(50, normalize=True)))
+        runs.append(rec)
+        eng.close()
+    for a, b in zip(*runs):
+        assert a[0] == b[0]
+        for x, y in zip(a[1:4], b[1:4]):
+            assert x.shape == y.shape and np.array_equal(x.view(np.uint64), y.view(np.uint64))
+        assert np.array_equal(a[4][0], b[4][0])
+        assert np.array_equal(a[4][1].view(np.uint64), b[4][1].view(np.uint64))
+    # parity of the first run with the oracle, batch by batch
+    r_o, _, _ = O.cpi(*cur, 0, C_RESTART, eps)
+    assert l1(runs[0][0][1], r_o) <= TOL[prec]
+    for ops, (st, r, *_rest) in zip(batches, runs[0][1:]):
+        assert g.apply(ops, protect=(0,)) == -1
+        new = g.csr()
+        force = st["iterations"] if prec == N.OSP_PREC_FP32_ACC64 else 0
+        r_o, q, _, _ = O.osp(cur, new, r_o, C_RESTART, eps, force_iters=force)
+        cur = new
+        assert st["qoff_l1"] == pytest.approx(np.abs(q).sum(), rel=1e-6, abs=1e-15)
+        assert l1(r, r_o) <= TOL[prec]
+
+
+def test_deterministic_mode_is_for_one_seed():
+    src, dst = W.er_graph(500, 4000, 2)
+    eng = N.Engine(precision=N.OSP_PREC_FP64, device=0, deterministic=True)
+    eng.load_graph(500, src, dst)
+    with pytest.raises(N.OspError) as err:
+        eng.set_seeds([0, 1], C_RESTART)
+    assert err.value.status == N.OSP_ENOTSUP
+    eng.close()
