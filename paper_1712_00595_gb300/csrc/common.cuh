@@ -87,6 +87,9 @@ struct Multi {
   int S, Sp, K;
   int KG;              // columns per lane in a column group of the batch kernel
   int KG_init;         // ... of the initial CPI (float rows when batches use bf16)
+  int pack;            // 1: bf16 32-column groups take their columns through slot_col (set per launch)
+  int* slot_col;       // [Sp] packed groups: column held by group slot q (chosen at each x(0))
+  int* col_slot;       // [Sp] its inverse
   int* seeds;          // [S] internal ids, by column
   double* r;           // [nc Sp] scores (unnormalised r_temp)
   double* xacc;        // [nc Sp] offset accumulator

@@ -537,8 +537,14 @@ osp_status enqueue_propagate(osp_ctx* ctx, const PropParams& pp, bool init) {
     const int KG = as_init ? ctx->d.mu.KG_init : ctx->d.mu.KG;
     PropParams p = pp;
     p.hot_n = hot_rows(ctx, prec, KG);
-    CK(launch_propagate_multi(ctx->d, p, prec, KG, as_init ? ctx->grid_multi_init : ctx->grid_multi,
-                              seed_bulk(ctx, prec, KG), ctx->stream));
+    const bool bulk = seed_bulk(ctx, prec, KG);
+    Dev d = ctx->d;
+    // bf16 32-column groups gathered by teams: the columns are packed into
+    // groups per call, largest offsets first, so that the columns still running
+    // after the first steps share few groups
+    d.mu.pack = prec == OSP_PREC_BF16_ACC64 && KG == 1 && !bulk && d.mu.Sp > 32;
+    CK(launch_propagate_multi(d, p, prec, KG, as_init ? ctx->grid_multi_init : ctx->grid_multi,
+                              bulk, ctx->stream));
   }
   else
     CK(launch_propagate(ctx->d, pp, ctx->grid_prop, ctx->stream));
@@ -1221,6 +1227,8 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     ML(M.col_last, 32 * K);
     ML(M.res_bound, 32 * K);
     ML(M.force, 32 * K);
+    ML(M.slot_col, 32 * K);
+    ML(M.col_slot, 32 * K);
     ML(hub, nh * 32 * K);
     ML(M.hub_cnt, nh * 8);
 #undef ML

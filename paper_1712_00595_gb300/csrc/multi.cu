@@ -495,8 +495,10 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
   Ctl* ctl = d.ctl;
   __shared__ double s_max[kPropThreads / 32];
   __shared__ double s_sum[kPropThreads];
+  __shared__ double s_key[kMaxSeeds];
   __shared__ unsigned s_gmask;
   if (threadIdx.x == 0) s_gmask = 0;
+  const bool pack = M.pack != 0 && KG == 1;
   // thread t sums column t % Sp over the CTAs b = t / Sp (mod Q) with eight
   // independent accumulators; the Q slices are then added in a fixed order
   const int Q = (int)blockDim.x / Sp;
@@ -532,11 +534,13 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
       if (L == 0.0 && f == 0) {
         M.col_iters[j] = 1;
         M.active[j] = 0;
+        if (pack) s_key[j] = -1.0;
       } else {
         M.col_iters[j] = 0;
         M.active[j] = 1;
         live = 1;
-        atomicOr(&s_gmask, 1u << (j / G));
+        if (pack) s_key[j] = f > 0 ? 1e300 : L;  // forced columns run longest
+        else atomicOr(&s_gmask, 1u << (j / G));
       }
     } else if (*(volatile int*)&M.active[j]) {
       M.col_iters[j] = it;
@@ -553,8 +557,26 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
         M.res_bound[j] += (1.0 - ctl->c) * L;
       } else {
         live = 1;
-        atomicOr(&s_gmask, 1u << (j / G));
+        atomicOr(&s_gmask, 1u << ((pack ? __ldcg(M.col_slot + j) : j) / G));
       }
+    }
+  }
+  if (pack && it == 0) {
+    // group slots by decreasing ||x(0)||_1 (ties by column), columns without
+    // an offset last; a column's slot is its rank
+    for (int j = threadIdx.x; j < Sp; j += blockDim.x)
+      if (j >= M.S) s_key[j] = -2.0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
+      const double kj = s_key[j];
+      int rank = 0;
+      for (int i = 0; i < Sp; ++i) {
+        const double ki = s_key[i];
+        rank += ki > kj || (ki == kj && i < j);
+      }
+      M.slot_col[rank] = j;
+      M.col_slot[j] = rank;
+      if (kj >= 0.0) atomicOr(&s_gmask, 1u << (rank / G));
     }
   }
   seen = warp_max(seen);
@@ -987,6 +1009,10 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   }
   const Multi& M = d.mu;
   const int Sp = M.Sp;
+  // packed groups (bf16 team path): group slot q holds column slot_col[q],
+  // chosen per call by the x(0) decision so that columns likely to run long
+  // share groups; R, the offsets and the per-column state stay by column
+  const bool pack = kTeam && M.pack != 0;
   const size_t gs = (size_t)d.nc * G;  // gather block: elements per column group
   const int n = ctl->n;
   const long long m = ctl->m;
@@ -1020,7 +1046,83 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   // x(0): stamped rows move from xacc into R and, scaled, into y(0); every
   // node with out-edges gets its y(0) row (zero when not stamped) in each
   // column group that has a nonzero offset entry
-  {
+  if (pack) {
+    // 1. ||x(0)||_1 per column from the stamped rows; the decision orders the
+    //    columns by it (largest first: a larger offset needs more steps) into
+    //    group slots and picks the groups that hold a running column
+    for (int j = lane; j < Sp; j += 32) my_part[j] = 0.0;
+    unsigned tb = 0;  // bit k: column lane + 32 k has an offset entry
+    for (int k = 0; k < 8 && lane + 32 * k < M.S; ++k)
+      if (*(volatile int*)&M.touched[lane + 32 * k]) tb |= 1u << k;
+    __syncthreads();
+    for (int vb = gw * 32; vb < n && __any_sync(0xffffffffu, tb != 0); vb += nw * 32) {
+      const int vl = vb + lane;
+      unsigned stamped = __ballot_sync(0xffffffffu, vl < n && __ldcg(d.mark + vl) == epoch);
+      while (stamped) {
+        const int v = vb + __ffs(stamped) - 1;
+        stamped &= stamped - 1;
+        for (unsigned t = tb; t; t &= t - 1) {
+          const int j = lane + 32 * (__ffs(t) - 1);
+          my_part[j] += fabs(__ldcg(M.xacc + (size_t)v * Sp + j));
+        }
+      }
+    }
+    column_sums();
+    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, 0, m);
+    if (!bar_release(ctl, sh)) return;
+    // 2. R += x(0) and the y(0) rows, in group slots
+    if (threadIdx.x < 8) s_grp[threadIdx.x] = *(volatile int*)&ctl->grp[threadIdx.x];
+    if (threadIdx.x == 0) s_ngrp = *(volatile int*)&ctl->n_grp;
+    __syncthreads();
+    const int ng = s_ngrp;
+    int colg[8];
+    unsigned actg = 0;  // bit gi: this lane's column of group s_grp[gi] runs
+#pragma unroll
+    for (int gi = 0; gi < 8; ++gi) {
+      colg[gi] = 0;
+      if (gi < ng) {
+        colg[gi] = __ldcg(M.slot_col + s_grp[gi] * G + lane);
+        if (*(volatile int*)&M.active[colg[gi]]) actg |= 1u << gi;
+      }
+    }
+    for (int vb = gw * 32; vb < n && ng > 0; vb += nw * 32) {
+      const int vl = vb + lane;
+      const unsigned stamped = __ballot_sync(0xffffffffu, vl < n && __ldcg(d.mark + vl) == epoch);
+      const A s_l = vl < n ? scale_of<A>(d, vl) : (A)0;
+      unsigned work = stamped | __ballot_sync(0xffffffffu, s_l != (A)0);
+      while (work) {
+        const int jj = __ffs(work) - 1;
+        work &= work - 1;
+        const int v = vb + jj;
+        const bool st = (stamped >> jj) & 1u;
+        const A s = __shfl_sync(0xffffffffu, s_l, jj);
+#pragma unroll
+        for (int gi = 0; gi < 8; ++gi) {
+          if (gi >= ng || !((actg >> gi) & 1u)) continue;
+          const size_t ybase = s_grp[gi] * gs + (size_t)v * G + lane;
+          TY yv = from_acc((A)0, (TY*)nullptr), ev = yv;
+          if (st) {
+            const size_t rb = (size_t)v * Sp + colg[gi];
+            const double x = __ldcg(M.xacc + rb);
+            if (x != 0.0) {
+              M.r[rb] += x;
+              M.xacc[rb] = 0.0;
+              const A w = (A)((A)x * s);
+              yv = from_acc(w, (TY*)nullptr);
+              if constexpr (FB) ev = __float2bfloat16_rn(w - __bfloat162float(yv));
+            }
+          }
+          if (s != (A)0) {
+            const TY y1[1] = {yv}, e1[1] = {ev};
+            st_pol(yb[0] + ybase, y1, pol.once);
+            if constexpr (FB) st_pol(eb + ybase, e1, pol.once);
+          }
+        }
+      }
+    }
+    if (bar_arrive(ctl, sh) && threadIdx.x == 0) ctl->ctr[1] = 0;
+    if (!bar_release(ctl, sh)) return;
+  } else {
     if (threadIdx.x == 0) s_tmask = 0;
     for (int j = lane; j < Sp; j += 32) my_part[j] = 0.0;
     __syncthreads();
@@ -1100,6 +1202,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
     const int n_items = n_pieces + n_tasks;
     const long long total = (long long)s_ngrp * n_items;
     int cur = -1;  // column group of the items this warp works on now
+    int pcol = -1;  // packed bf16 groups: this lane's column in group cur
     unsigned act = 0;
     bool on4 = false;
     double l1[KG];
@@ -1109,7 +1212,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       if (cur >= 0) {
 #pragma unroll
         for (int k = 0; k < KG; ++k) {
-          my_part[cur * G + lane * KG + k] += l1[k];
+          my_part[(kTeam && pack ? pcol : cur * G + lane * KG) + k] += l1[k];
           l1[k] = 0.0;
         }
       }
@@ -1126,9 +1229,11 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
         flush();
         cur = g;
         act = 0;
+        if constexpr (kTeam) pcol = pack ? __ldcg(M.slot_col + g * G + lane) : g * G + lane;
 #pragma unroll
         for (int k = 0; k < KG; ++k)
-          act |= (unsigned)(*(volatile int*)&M.active[g * G + lane * KG + k] != 0) << k;
+          act |= (unsigned)(*(volatile int*)&M.active[(kTeam ? pcol : g * G + lane * KG) + k] != 0)
+                 << k;
         if constexpr (kTeam) {
           // team gathers: lane (t, s) loads columns [4 s, 4 s + 4) of a row
           const unsigned am = __ballot_sync(0xffffffffu, act != 0);
@@ -1137,8 +1242,9 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       }
       const TY* ysg = ys + g * gs;           // the group's gather rows, G elements apart
       const TY* ysl = ysg + lane * KG;       // this lane's columns of them
-      const size_t c0 = (size_t)g * G + lane * KG;
-      auto rbase_of = [&](int v) { return (size_t)v * Sp + c0; };
+      const size_t c0 = (size_t)g * G + lane * KG;  // slot: gather rows, residuals, hub sums
+      const size_t rc0 = kTeam ? (size_t)pcol : c0;  // column of R
+      auto rbase_of = [&](int v) { return (size_t)v * Sp + rc0; };
       auto ybase_of = [&](int v) { return g * gs + (size_t)v * G + lane * KG; };
       if (ti < n_pieces) {
         // a piece of a long in-list; the piece that completes the list finishes it
