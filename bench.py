@@ -958,6 +958,7 @@ def run_serve(args, rank, world, n_req=4000):
         "latency": {"update": upd, "query": qry},
         "offered_seconds": timed[-1].t, "served_seconds": wall,
         "engine_batches": len(sizes_b),
+        "topk_seeds": {"ranked": srv.topk_computed, "reused_same_version": srv.topk_reused},
         "ops_per_batch_mean": float(np.mean(sizes_b)) if sizes_b else 0.0,
     }
 

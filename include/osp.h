@@ -235,11 +235,16 @@ osp_status osp_apply_updates_device(osp_ctx *ctx, const osp_update *ops_device, 
 
 /* Largest U applied as one unit (16,384): an invalid op leaves the state
  * unchanged. Apply calls accept up to 2^22 ops; a larger batch is ingested
- * and merged in consecutive sub-batches of osp_max_batch() ops, all against
- * the same r_old (their offsets add up to the whole batch's offset), followed
- * by one propagation. If an op of a later sub-batch is invalid, the
+ * and merged in sub-batches of at most osp_max_batch() ops, all against the
+ * same r_old (their offsets add up to the whole batch's offset), followed by
+ * one propagation. Sub-batches are consecutive runs of the batch, except for
+ * a host batch of edge insertions and deletions only, with every id below
+ * the node count: its ops are then ordered by source node (ops of one node
+ * keep their order; ops of different nodes commute) and each sub-batch takes
+ * whole source nodes, so that a node's out-list changes, and its offset terms
+ * are formed, once per call. If an op of a later sub-batch is invalid, the
  * sub-batches before it stay applied and propagated, the call returns
- * OSP_EINVAL and stats->bad_op gives the op's index. */
+ * OSP_EINVAL and stats->bad_op gives the op's index in the caller's batch. */
 int64_t osp_max_batch(void);
 
 /* Copy the scores of seed seed_idx to out[0 .. n) (host). normalize != 0 returns
@@ -297,7 +302,8 @@ osp_status osp_topk_noalloc(const double *scores_device, int64_t n, int32_t k, i
 /* Query slots for serving: queries that overlap on the device with the next
  * update batch. Allocates nslots (0 <= nslots <= 64; 0 frees them) slots, each
  * with its own top-k scratch and an n-double column buffer (about 8 bytes per
- * node slot plus 150 KB, so the HBM budget for queries sets nslots), and a
+ * node slot plus 130 KB of device memory, so the HBM budget for queries sets
+ * nslots; plus 48 KB of host-mapped pinned memory for the result), and a
  * second CUDA stream for them. A query enqueued with osp_topk_async reads the
  * scores as of the last completed init/apply call; the ingest, merge and
  * offset kernels of the next apply run alongside it, and that call's
@@ -309,8 +315,19 @@ osp_status osp_query_slots(osp_ctx *ctx, int32_t nslots);
  * without waiting. OSP_ESTATE if the slot still holds a query. */
 osp_status osp_topk_async(osp_ctx *ctx, int32_t slot, int32_t seed_idx, int32_t k, int normalize);
 
+/* Enqueue the top-k of m seeds (1 <= m <= 32; seed seed_idx[i] in slot
+ * slots[i], slots distinct and free) as one launch sequence on the query
+ * stream and return without waiting; collect each slot with osp_topk_wait.
+ * Same results as m calls of osp_topk_async. OSP_EINVAL on a bad slot, seed,
+ * k or count, OSP_ESTATE if a slot still holds a query; nothing is enqueued
+ * then. */
+osp_status osp_topk_async_many(osp_ctx *ctx, const int32_t *slots, const int32_t *seed_idx,
+                               int32_t m, int32_t k, int normalize);
+
 /* Wait for the slot's query and copy its result (host arrays of k entries,
- * count in *k_out); the slot is free again afterwards. */
+ * count in *k_out); the slot is free again afterwards. The kernels write the
+ * result to host-mapped memory of the slot, so this is a wait and a host
+ * copy. */
 osp_status osp_topk_wait(osp_ctx *ctx, int32_t slot, int32_t *ids, double *scores, int32_t *k_out);
 
 /* Copy the current graph as sorted adjacency (host arrays): direction 0 gives

@@ -173,6 +173,30 @@ struct TopkState {
   int bin_count;              // keys inside the bin
   int keep;                   // bin keys kept (all, or the k_rem smallest ids of one key value)
   int pad;
+  unsigned long long kmin;    // smallest and largest key matching the prefix in the last pass
+  unsigned long long kmax;
+};
+
+// One top-k job: a score vector of n entries, its scratch, its outputs (device
+// or host-mapped memory). A launch serves up to kTopkMaxJobs of them.
+struct TopkJob {
+  const double* src;
+  TopkState* st;
+  unsigned* hist;            // [4096]
+  int* blk_a; int* blk_b;    // [n / kTopkChunk + 2]
+  unsigned long long* keys;  // [kTopkMaxK + kTopkCand]
+  int* ids;                  // [kTopkMaxK + kTopkCand]
+  const double* norm;        // ||src||_1 to divide the output scores by, or null
+  int* out_ids; double* out_sc; int* out_k;
+};
+constexpr int kTopkMaxJobs = 32;
+struct TopkJobs {  // passed by value (about 3 KB of kernel parameters)
+  int m, n, k, pad;
+  TopkJob j[kTopkMaxJobs];
+};
+struct GatherJobs {
+  int col[kTopkMaxJobs];
+  double* dst[kTopkMaxJobs];
 };
 
 struct PropParams {

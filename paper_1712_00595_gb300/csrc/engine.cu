@@ -33,6 +33,8 @@ struct HostCtlView {  // the leading fields of Ctl, read back after every call
 };
 
 constexpr int kMaxQuerySlots = 64;
+// host-mapped result block of a query slot: scores, ids, count
+constexpr size_t kSlotHostBytes = (sizeof(double) + sizeof(int)) * kTopkMaxK + 64;
 
 // Device scratch of one top-k query.
 struct TopkScratch {
@@ -51,7 +53,8 @@ struct TopkScratch {
 // A query slot: its own scratch and column buffer, so that queries in flight on
 // the query stream do not share memory with each other or with the engine.
 struct QuerySlot {
-  TopkScratch t{};
+  TopkScratch t{};       // out_* point into host_out (host-mapped pinned memory)
+  void* host_out = nullptr;
   double* col = nullptr;
   cudaEvent_t done = nullptr;
   int busy = 0;
@@ -189,8 +192,10 @@ void drop_graphs(osp_ctx* ctx) {
 
 void free_slots(osp_ctx* ctx) {
   if (ctx->qstream) cudaStreamSynchronize(ctx->qstream);
-  for (auto& q : ctx->qslots)
+  for (auto& q : ctx->qslots) {
     if (q.done) cudaEventDestroy(q.done);
+    if (q.host_out) cudaFreeHost(q.host_out);
+  }
   ctx->qslots.clear();
   for (void* p : ctx->qallocs) dfree(ctx, p);
   ctx->qallocs.clear();
@@ -647,6 +652,61 @@ osp_status capture_graphs(osp_ctx* ctx, int Np, double eps, osp_ctx::GraphPair* 
 // follows. ops is a device pointer, or a host one when host != 0 (staged per
 // sub-batch through pinned memory). An invalid op stops the sequence: the
 // sub-batches before it stay applied and are propagated.
+// Sub-batches of a large host batch of edge ops only (ids in [0, n)): the ops
+// stably ordered by source row, whole rows packed into each sub-batch (a row
+// with more than kMaxBatch ops is cut), so that every changed row's offset is
+// formed once instead of once per sub-batch that edits it. Ops on one row keep
+// their order, and ops on different rows commute, so the final edge set is the
+// one of the batch in its own order. Returns false (and leaves perm empty) when
+// the batch holds another kind of op or an id out of range.
+bool group_by_row(const osp_update* ops, int64_t U, int64_t n, std::vector<int32_t>& perm,
+                  std::vector<int64_t>& cuts) {
+  perm.clear();
+  cuts.clear();
+  for (int64_t i = 0; i < U; ++i) {
+    const osp_update& o = ops[i];
+    if ((o.op != OSP_OP_INSERT_EDGE && o.op != OSP_OP_DELETE_EDGE) || o.u < 0 || o.u >= n ||
+        o.v < 0 || o.v >= n)
+      return false;
+  }
+  // LSD radix sort of the op indices by source row (stable), 11 bits a pass
+  std::vector<int32_t> a(U), b(U);
+  for (int64_t i = 0; i < U; ++i) a[i] = (int32_t)i;
+  int bits = 1;
+  while ((int64_t(1) << bits) < n) ++bits;
+  std::vector<int64_t> cnt(1 << 11);
+  for (int sh = 0; sh < bits; sh += 11) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t i = 0; i < U; ++i) ++cnt[(ops[a[i]].u >> sh) & 2047];
+    int64_t t = 0;
+    for (auto& c : cnt) {
+      const int64_t x = c;
+      c = t;
+      t += x;
+    }
+    for (int64_t i = 0; i < U; ++i) b[cnt[(ops[a[i]].u >> sh) & 2047]++] = a[i];
+    a.swap(b);
+  }
+  perm.swap(a);
+  cuts.push_back(0);
+  int64_t start = 0;  // of the open sub-batch
+  for (int64_t i = 0; i < U;) {
+    int64_t j = i;
+    while (j < U && ops[perm[j]].u == ops[perm[i]].u) ++j;
+    if (j - i > kMaxBatch) {  // a row alone above the limit: cut it
+      if (i > start) cuts.push_back(i);
+      for (int64_t c = i + kMaxBatch; c < j; c += kMaxBatch) cuts.push_back(c);
+      start = cuts.back();
+    } else if (j - start > kMaxBatch) {
+      cuts.push_back(i);
+      start = i;
+    }
+    i = j;
+  }
+  cuts.push_back(U);
+  return true;
+}
+
 osp_status apply_large(osp_ctx* ctx, const osp_update* ops, bool host, int64_t U, double eps,
                        osp_batch_stats* st) {
   if (!(eps > 0)) return fail(ctx, OSP_EINVAL, "eps must be > 0");
@@ -654,9 +714,18 @@ osp_status apply_large(osp_ctx* ctx, const osp_update* ops, bool host, int64_t U
   const int64_t m_before = ctx->m;
   int64_t bad = -1;
   osp_status err = OSP_OK;
+  std::vector<int32_t> perm;
+  std::vector<int64_t> cuts;
+  if (!(host && group_by_row(ops, U, ctx->n, perm, cuts))) {
+    perm.clear();
+    cuts.clear();
+    for (int64_t s0 = 0; s0 < U; s0 += kMaxBatch) cuts.push_back(s0);
+    cuts.push_back(U);
+  }
   CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-  for (int64_t s0 = 0; s0 < U; s0 += kMaxBatch) {
-    const int u = (int)std::min<int64_t>(kMaxBatch, U - s0);
+  for (size_t ci = 0; ci + 1 < cuts.size(); ++ci) {
+    const int64_t s0 = cuts[ci];
+    const int u = (int)(cuts[ci + 1] - s0);
     osp_status s = reserve_for_batch(ctx, u);
     if (s != OSP_OK) {
       err = s;
@@ -664,7 +733,12 @@ osp_status apply_large(osp_ctx* ctx, const osp_update* ops, bool host, int64_t U
     }
     const osp_update* p = ops + s0;
     if (host) {
-      std::memcpy(ctx->pinned, p, sizeof(osp_update) * (size_t)u);
+      osp_update* pin = (osp_update*)ctx->pinned;
+      if (perm.empty()) {
+        std::memcpy(pin, p, sizeof(osp_update) * (size_t)u);
+      } else {
+        for (int i = 0; i < u; ++i) pin[i] = ops[perm[s0 + i]];
+      }
       CK(cudaMemcpyAsync(ctx->ops_stage, ctx->pinned, sizeof(osp_update) * (size_t)u,
                          cudaMemcpyHostToDevice, ctx->stream));
       p = ctx->ops_stage;
@@ -677,7 +751,7 @@ osp_status apply_large(osp_ctx* ctx, const osp_update* ops, bool host, int64_t U
     s = read_ctl(ctx, &h);  // also orders the pinned buffer's reuse
     if (s != OSP_OK) return s;
     if (h.status == OSP_EINVAL) {
-      bad = s0 + h.bad_op;
+      bad = perm.empty() ? s0 + h.bad_op : (int64_t)perm[s0 + h.bad_op];
       h.status = 0;
       s = write_ctl(ctx, h);
       if (s != OSP_OK) return s;
@@ -754,46 +828,55 @@ osp_status apply_common(osp_ctx* ctx, const osp_update* ops_dev, int64_t U, doub
 int col_for(const osp_ctx* ctx, int j) { return ctx->S > 1 ? ctx->col_of[j] : j; }
 
 // Column col of the scores in caller order into dst, on stream st.
-osp_status enqueue_gather(osp_ctx* ctx, cudaStream_t st, int col, double* dst) {
+// Score columns in caller order into dsts[i] (device, n doubles each).
+osp_status enqueue_gather(osp_ctx* ctx, cudaStream_t st, const int* cols, double* const* dsts, int m) {
   const int n = (int)ctx->n;
-  if (ctx->S > 1)
-    k_gather_col<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.mu.r, ctx->d.mu.Sp, col, ctx->d.ext2int, n, dst);
-  else
-    k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dst);
-  ++ctx->launches;
+  if (ctx->S > 1) {
+    GatherJobs G{};
+    for (int i = 0; i < m; ++i) {
+      G.col[i] = cols[i];
+      G.dst[i] = dsts[i];
+    }
+    k_gather_cols<<<dim3(ctx->num_sms * 4, m), 256, 0, st>>>(ctx->d.mu.r, ctx->d.mu.Sp,
+                                                            ctx->d.int2ext, n, G);
+    ++ctx->launches;
+  } else {
+    for (int i = 0; i < m; ++i) {
+      k_gather_ext<<<ctx->num_sms * 4, 256, 0, st>>>(ctx->d.r, ctx->d.ext2int, n, dsts[i]);
+      ++ctx->launches;
+    }
+  }
   CK(cudaGetLastError());
   return OSP_OK;
 }
 
-// Top-k of rs[0 .. n) on stream st with scratch t: radix select, ordered
-// compaction, one-CTA sort (results in t.out_*).
-osp_status enqueue_topk(osp_ctx* ctx, cudaStream_t st, const double* rs, int n, int k,
-                        int normalize, const TopkScratch& t) {
-  const int g = ctx->num_sms * 4;
-  k_topk_reset<<<1, 1024, 0, st>>>(t.st, t.hist, k);
-  ++ctx->launches;
-  const int widths[6] = {12, 12, 12, 12, 12, 4};
-  for (int w : widths) {
-    k_topk_hist<<<g, 256, 0, st>>>(rs, n, t.st, t.hist, w);
-    ++ctx->launches;
-    k_topk_select<<<1, 1024, 0, st>>>(t.st, t.hist, w, kTopkCand);
-    ++ctx->launches;
-  }
-  const int nb = (n + kTopkChunk - 1) / kTopkChunk;
-  k_topk_count<<<nb, 1024, 0, st>>>(rs, n, t.st, t.blk_a, t.blk_b);
-  ++ctx->launches;
-  k_topk_scan<<<1, 32, 0, st>>>(t.st, t.blk_a, t.blk_b, nb, kTopkCand);
-  ++ctx->launches;
-  k_topk_emit<<<nb, 1024, 0, st>>>(rs, n, t.st, t.blk_a, t.blk_b, t.keys, t.ids);
-  ++ctx->launches;
-  if (normalize) {
-    k_abs_sum<<<abs_grid(ctx), 256, 0, st>>>(rs, n, t.dsum, t.dsum + 1);
-    ++ctx->launches;
-  }
-  const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
-  k_topk_sort<<<1, 1024, smem, st>>>(rs, t.st, t.keys, t.ids, kTopkMaxK + kTopkCand, k,
-                                     normalize ? t.dsum : nullptr, t.out_ids, t.out_sc, t.out_k);
-  ++ctx->launches;
+TopkJob topk_job(const double* src, const TopkScratch& t, bool normalize) {
+  TopkJob j{};
+  j.src = src;
+  j.st = t.st;
+  j.hist = t.hist;
+  j.blk_a = t.blk_a;
+  j.blk_b = t.blk_b;
+  j.keys = t.keys;
+  j.ids = t.ids;
+  j.norm = normalize ? t.dsum : nullptr;
+  j.out_ids = t.out_ids;
+  j.out_sc = t.out_sc;
+  j.out_k = t.out_k;
+  return j;
+}
+
+// Top-k of every job of J on stream st: the norms asked for, the radix
+// select and ordered compaction, the sort (results in each job's out_*).
+osp_status enqueue_topk(osp_ctx* ctx, cudaStream_t st, const TopkJobs& J) {
+  for (int i = 0; i < J.m; ++i)
+    if (J.j[i].norm) {
+      double* sum = const_cast<double*>(J.j[i].norm);
+      k_abs_sum<<<abs_grid(ctx), 256, 0, st>>>(J.j[i].src, J.n, sum, sum + 1);
+      ++ctx->launches;
+    }
+  ctx->launches += enqueue_topk_select(J, ctx->num_sms, st);
+  ctx->launches += enqueue_topk_sort(J, st);
   CK(cudaGetLastError());
   return OSP_OK;
 }
@@ -896,7 +979,7 @@ osp_status osp_create(osp_ctx** out, const osp_options* opt) {
     e = cudaFuncSetAttribute(k_ingest, cudaFuncAttributeMaxDynamicSharedMemorySize, kIngestSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (kTopkMaxK + kTopkCand) * (int)(sizeof(unsigned long long) + sizeof(int)));
+                             kTopkSortSmem);
   if (e != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -1434,11 +1517,18 @@ osp_status osp_topk(osp_ctx* ctx, int32_t seed_idx, int32_t k, int normalize, in
     return fail(ctx, OSP_EINVAL, "bad seed index, k outside [1, 4096] or null output");
   cudaStream_t st = ctx->stream;
   // rank the scores in caller order, so that ties go to the smaller caller id
-  s = enqueue_gather(ctx, st, col_for(ctx, seed_idx), ctx->dtmp);
+  const int col = col_for(ctx, seed_idx);
+  double* dst = ctx->dtmp;
+  s = enqueue_gather(ctx, st, &col, &dst, 1);
   if (s != OSP_OK) return s;
   const TopkScratch t{ctx->tk_state, ctx->tk_hist, ctx->tk_blk_a, ctx->tk_blk_b, ctx->tk_keys,
                       ctx->tk_ids, ctx->tk_out_ids, ctx->tk_out_sc, ctx->tk_out_k, ctx->dsum};
-  s = enqueue_topk(ctx, st, ctx->dtmp, (int)ctx->n, k, normalize, t);
+  TopkJobs J{};
+  J.m = 1;
+  J.n = (int)ctx->n;
+  J.k = k;
+  J.j[0] = topk_job(ctx->dtmp, t, normalize != 0);
+  s = enqueue_topk(ctx, st, J);
   if (s != OSP_OK) return s;
   CK(cudaMemcpyAsync(k_out, ctx->tk_out_k, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ids, ctx->tk_out_ids, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
@@ -1481,35 +1571,67 @@ osp_status osp_query_slots(osp_ctx* ctx, int32_t nslots) {
     QL(t.blk_b, nc / kTopkChunk + 2);
     QL(t.keys, kTopkMaxK + kTopkCand);
     QL(t.ids, kTopkMaxK + kTopkCand);
-    QL(t.out_ids, kTopkMaxK);
-    QL(t.out_sc, kTopkMaxK);
-    QL(t.out_k, 1);
     QL(t.dsum, kAbsParts + 2);
 #undef QL
+    // results go straight to host-mapped memory: collecting them is a wait
+    // and a host copy, with no device-to-host transfer call
+    CK(cudaHostAlloc(&q.host_out, kSlotHostBytes, cudaHostAllocMapped));
+    void* dev = nullptr;
+    CK(cudaHostGetDevicePointer(&dev, q.host_out, 0));
+    t.out_sc = (double*)dev;
+    t.out_ids = (int*)((char*)dev + sizeof(double) * kTopkMaxK);
+    t.out_k = t.out_ids + kTopkMaxK;
     CK(cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return OSP_OK;
 }
 
-osp_status osp_topk_async(osp_ctx* ctx, int32_t slot, int32_t seed_idx, int32_t k, int normalize) {
+osp_status osp_topk_async_many(osp_ctx* ctx, const int32_t* slots, const int32_t* seed_idx,
+                               int32_t m, int32_t k, int normalize) {
   osp_status s = check_ready(ctx, true);
   if (s != OSP_OK) return s;
-  if (slot < 0 || slot >= (int)ctx->qslots.size()) return fail(ctx, OSP_EINVAL, "no such query slot");
-  QuerySlot& q = ctx->qslots[slot];
-  if (q.busy) return fail(ctx, OSP_ESTATE, "query slot busy (collect it with osp_topk_wait)");
-  if (seed_idx < 0 || seed_idx >= ctx->S || k <= 0 || k > kTopkMaxK)
-    return fail(ctx, OSP_EINVAL, "bad seed index or k outside [1, 4096]");
+  if (m < 1 || m > kTopkMaxJobs || !slots || !seed_idx)
+    return fail(ctx, OSP_EINVAL, "between 1 and 32 queries per call, non-null arrays");
+  if (k <= 0 || k > kTopkMaxK) return fail(ctx, OSP_EINVAL, "k outside [1, 4096]");
+  for (int i = 0; i < m; ++i) {
+    if (slots[i] < 0 || slots[i] >= (int)ctx->qslots.size())
+      return fail(ctx, OSP_EINVAL, "no such query slot");
+    if (ctx->qslots[slots[i]].busy)
+      return fail(ctx, OSP_ESTATE, "query slot busy (collect it with osp_topk_wait)");
+    for (int j = 0; j < i; ++j)
+      if (slots[j] == slots[i]) return fail(ctx, OSP_EINVAL, "a slot named twice");
+    if (seed_idx[i] < 0 || seed_idx[i] >= ctx->S) return fail(ctx, OSP_EINVAL, "bad seed index");
+  }
   cudaStream_t qs = ctx->qstream;
   CK(cudaStreamWaitEvent(qs, ctx->ev_scores, 0));
-  s = enqueue_gather(ctx, qs, col_for(ctx, seed_idx), q.col);
-  if (s == OSP_OK) s = enqueue_topk(ctx, qs, q.col, (int)ctx->n, k, normalize, q.t);
+  int cols[kTopkMaxJobs];
+  double* dsts[kTopkMaxJobs];
+  TopkJobs J{};
+  J.m = m;
+  J.n = (int)ctx->n;
+  J.k = k;
+  for (int i = 0; i < m; ++i) {
+    QuerySlot& q = ctx->qslots[slots[i]];
+    cols[i] = col_for(ctx, seed_idx[i]);
+    dsts[i] = q.col;
+    J.j[i] = topk_job(q.col, q.t, normalize != 0);
+  }
+  s = enqueue_gather(ctx, qs, cols, dsts, m);
+  if (s == OSP_OK) s = enqueue_topk(ctx, qs, J);
   if (s != OSP_OK) return s;
-  CK(cudaEventRecord(q.done, qs));
+  for (int i = 0; i < m; ++i) {
+    QuerySlot& q = ctx->qslots[slots[i]];
+    CK(cudaEventRecord(q.done, qs));
+    q.busy = 1;
+    q.k = k;
+  }
   CK(cudaEventRecord(ctx->ev_queries, qs));
-  q.busy = 1;
-  q.k = k;
   return OSP_OK;
+}
+
+osp_status osp_topk_async(osp_ctx* ctx, int32_t slot, int32_t seed_idx, int32_t k, int normalize) {
+  return osp_topk_async_many(ctx, &slot, &seed_idx, 1, k, normalize);
 }
 
 osp_status osp_topk_wait(osp_ctx* ctx, int32_t slot, int32_t* ids, double* scores, int32_t* k_out) {
@@ -1521,10 +1643,11 @@ osp_status osp_topk_wait(osp_ctx* ctx, int32_t slot, int32_t* ids, double* score
   CK(cudaSetDevice(ctx->device));
   CK(cudaEventSynchronize(q.done));
   q.busy = 0;
-  int kk = 0;
-  CK(cudaMemcpy(&kk, q.t.out_k, sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(ids, q.t.out_ids, sizeof(int) * kk, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(scores, q.t.out_sc, sizeof(double) * kk, cudaMemcpyDeviceToHost));
+  const double* sc = (const double*)q.host_out;
+  const int* id = (const int*)(sc + kTopkMaxK);
+  const int kk = id[kTopkMaxK];
+  std::memcpy(ids, id, sizeof(int) * kk);
+  std::memcpy(scores, sc, sizeof(double) * kk);
   *k_out = kk;
   return OSP_OK;
 }

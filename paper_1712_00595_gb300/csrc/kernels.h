@@ -28,24 +28,19 @@ __global__ void k_gather_ext(const double* __restrict__ r, const int* __restrict
                              double* out);
 __global__ void k_scale_copy(const double* r, int n, const double* __restrict__ sum, double* out);
 
-// Top-k (radix select + ordered compaction + one-CTA bitonic sort)
-__global__ void k_topk_reset(TopkState* st, unsigned* hist, int k);
-__global__ void k_topk_hist(const double* __restrict__ r, int n, const TopkState* __restrict__ st,
-                            unsigned* hist, int width);
-__global__ void k_topk_select(TopkState* st, unsigned* hist, int width, int cand_max);
-__global__ void k_topk_count(const double* __restrict__ r, int n, const TopkState* __restrict__ st,
-                             int* blk_above, int* blk_bin);
-__global__ void k_topk_scan(TopkState* st, int* blk_above, int* blk_bin, int nb, int cand_max);
-__global__ void k_topk_emit(const double* __restrict__ r, int n, const TopkState* __restrict__ st,
-                            const int* __restrict__ blk_above, const int* __restrict__ blk_bin,
-                            unsigned long long* keys, int* ids);
-__global__ void k_topk_sort(const double* __restrict__ r, const TopkState* __restrict__ st,
-                            const unsigned long long* keys, const int* ids, int cap, int k,
-                            const double* __restrict__ norm, int* out_ids, double* out_scores,
-                            int* out_k);
+// Top-k (radix select + ordered compaction + one-CTA bitonic sort) over a job
+// table: enqueue_topk_select runs the selection and compaction (16 launches),
+// enqueue_topk_sort the final sort (k_topk_sort needs the dynamic shared
+// memory attribute set to kTopkSortSmem). Both return their launch counts.
+__global__ void k_topk_sort(TopkJobs J, int cap);
+__global__ void k_gather_cols(const double* __restrict__ r, int Sp, const int* __restrict__ int2ext,
+                              int n, GatherJobs G);
+int enqueue_topk_select(const TopkJobs& J, int num_sms, cudaStream_t st);
+int enqueue_topk_sort(const TopkJobs& J, cudaStream_t st);
 constexpr int kTopkMaxK = 4096;
 constexpr int kTopkCand = 4096;
 constexpr int kTopkChunk = 4096;
+constexpr int kTopkSortSmem = (kTopkMaxK + kTopkCand) * (int)(sizeof(unsigned long long) + sizeof(int));
 
 // Propagation (persistent, cooperative launch). T = double or float.
 template <typename T>

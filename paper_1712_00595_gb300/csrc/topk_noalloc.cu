@@ -58,9 +58,8 @@ osp_status device_setup(int dev, unsigned char** base, int* num_sms) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return OSP_ECUDA;
-    const int smem = (kTopkMaxK + kTopkCand) * (int)(sizeof(unsigned long long) + sizeof(int));
-    if (cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kTopkSortSmem) != cudaSuccess)
       return OSP_ECUDA;
     s.base = (unsigned char*)p;
     s.num_sms = sms;
@@ -105,23 +104,27 @@ extern "C" osp_status osp_topk_noalloc(const double* scores_device, int64_t n, i
 
   // k_topk_reset clears the state and the histogram; the per-chunk counts are
   // written whole by k_topk_count; only the norm accumulator is cleared here.
-  k_topk_reset<<<1, 1024, 0, st>>>(state, hist, k);
-  const int widths[6] = {12, 12, 12, 12, 12, 4};
-  for (int w : widths) {
-    k_topk_hist<<<sms * 4, 256, 0, st>>>(scores_device, nn, state, hist, w);
-    k_topk_select<<<1, 1024, 0, st>>>(state, hist, w, kTopkCand);
-  }
-  const int nb = (nn + kTopkChunk - 1) / kTopkChunk;
-  k_topk_count<<<nb, 1024, 0, st>>>(scores_device, nn, state, blk_a, blk_b);
-  k_topk_scan<<<1, 32, 0, st>>>(state, blk_a, blk_b, nb, kTopkCand);
-  k_topk_emit<<<nb, 1024, 0, st>>>(scores_device, nn, state, blk_a, blk_b, keys, ids);
+  TopkJobs J{};
+  J.m = 1;
+  J.n = nn;
+  J.k = k;
+  TopkJob& jb = J.j[0];
+  jb.src = scores_device;
+  jb.st = state;
+  jb.hist = hist;
+  jb.blk_a = blk_a;
+  jb.blk_b = blk_b;
+  jb.keys = keys;
+  jb.ids = ids;
+  jb.norm = normalize ? sum : nullptr;
+  jb.out_ids = ids_device;
+  jb.out_sc = out_scores_device;
+  jb.out_k = k_out_device;
   if (normalize) {
     if (cudaMemsetAsync(sum, 0, sizeof(double), st) != cudaSuccess) return OSP_ECUDA;
     k_abs_sum<<<sms * 2, 256, 0, st>>>(scores_device, nn, sum, nullptr);
   }
-  const size_t smem = (size_t)(kTopkMaxK + kTopkCand) * (sizeof(unsigned long long) + sizeof(int));
-  k_topk_sort<<<1, 1024, smem, st>>>(scores_device, state, keys, ids, kTopkMaxK + kTopkCand, k,
-                                     normalize ? sum : nullptr, ids_device, out_scores_device,
-                                     k_out_device);
+  enqueue_topk_select(J, sms, st);
+  enqueue_topk_sort(J, st);
   return cudaGetLastError() == cudaSuccess ? OSP_OK : OSP_ECUDA;
 }

@@ -33,7 +33,7 @@ EXPORTED = [
     "osp_get_l1_history", "osp_get_step_times", "osp_set_fixed_iterations", "osp_last_error",
     "osp_status_string", "osp_topk_noalloc", "osp_get_seed_stats",
     "osp_set_seed_iterations", "osp_get_schedule", "osp_query_slots", "osp_topk_async",
-    "osp_topk_wait", "osp_selftest_wait", "osp_num_nodes", "osp_get_residual_bounds",
+    "osp_topk_async_many", "osp_topk_wait", "osp_selftest_wait", "osp_num_nodes", "osp_get_residual_bounds",
     "osp_device_bytes",
 ]
 
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
             "osp_get_schedule": (C.c_int, [P, P]),
             "osp_query_slots": (C.c_int, [P, i32]),
             "osp_topk_async": (C.c_int, [P, i32, i32, i32, C.c_int]),
+            "osp_topk_async_many": (C.c_int, [P, P, P, i32, i32, C.c_int]),
             "osp_topk_wait": (C.c_int, [P, i32, P, P, P]),
             "osp_selftest_wait": (C.c_int, [i32, i32, i32]),
             "osp_num_nodes": (i64, [P]),
@@ -298,6 +299,16 @@ class Engine:
     def topk_async(self, slot, k, seed_idx=0, normalize=False):
         return self._check(self._L.osp_topk_async(self._h, int(slot), int(seed_idx), int(k),
                                                   int(bool(normalize))))
+
+    def topk_async_many(self, slots, seed_idx, k, normalize=False):
+        """One launch sequence for the top-k of several seeds, seed_idx[i] in
+        slots[i] (at most 32); collect each slot with topk_wait."""
+        sl = np.ascontiguousarray(slots, np.int32)
+        sd = np.ascontiguousarray(seed_idx, np.int32)
+        if sl.size != sd.size:
+            raise ValueError("one slot per seed")
+        return self._check(self._L.osp_topk_async_many(self._h, _ptr(sl), _ptr(sd), int(sl.size),
+                                                       int(k), int(bool(normalize))))
 
     def topk_wait(self, slot, k_max=4096):
         ids = np.empty(k_max, np.int32)

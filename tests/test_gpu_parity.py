@@ -280,6 +280,54 @@ def test_autotuned_schedule_gives_the_same_scores(seeds):
         assert l1(a, b) <= 1e-12
 
 
+@pytest.mark.parametrize("seeds", [[0], [0, 5, 77, 310]])
+def test_large_edge_batch_grouped_by_source_row(seeds):
+    """A host batch of edge ops above osp_max_batch() is cut by source row: one
+    row with more ops than a sub-batch holds (cut across sub-batches, order
+    kept), re-insertions and deletions of the same edge in one batch, and
+    random edits elsewhere. The graph equals the oracle's after the batch in
+    the caller's order and the scores equal the oracle's OSP."""
+    rng = np.random.default_rng(72)
+    n = 30000
+    src, dst = W.er_graph(n, 240000, 9)
+    ops = []
+    # row 3: 20,000 insertions, then half of them deleted again, then some re-inserted
+    tgt = rng.choice(np.arange(4, n), 20000, replace=False)
+    ops += [(3, int(v), W.OP_INSERT_EDGE) for v in tgt]
+    ops += [(3, int(v), W.OP_DELETE_EDGE) for v in tgt[::2]]
+    ops += [(3, int(v), W.OP_INSERT_EDGE) for v in tgt[::8]]
+    es = set(zip(src.tolist(), dst.tolist()))
+    for _ in range(30000):
+        u, v = int(rng.integers(0, n)), int(rng.integers(0, n))
+        if u == 3 or u == v:
+            continue
+        ops.append((u, v, W.OP_DELETE_EDGE if (u, v) in es and rng.random() < 0.7
+                    else W.OP_INSERT_EDGE))
+    order = rng.permutation(len(ops))
+    batch = np.zeros(len(ops), W.UPDATE_DTYPE)
+    for i, k in enumerate(order):  # interleave the rows, keeping row 3's own order
+        batch[i] = ops[k]
+    r3 = np.flatnonzero(batch["u"] == 3)
+    batch[r3] = np.array([o for o in ops if o[0] == 3], dtype=W.UPDATE_DTYPE)
+    assert batch.size > 3 * 16384
+    prec = N.OSP_PREC_FP64
+    eng = N.Engine(precision=prec, device=0)
+    eng.load_graph(n, src, dst)
+    eng.set_seeds(np.array(seeds, np.int32), C_RESTART)
+    eng.init_scores(1e-13)
+    g = O.Graph(n, src, dst)
+    cur = g.csr()
+    st = eng.apply_updates(batch, 1e-13)
+    assert g.apply(batch, protect=tuple(seeds)) == -1
+    new = g.csr()
+    check_graph(eng, g)
+    for j, s in enumerate(seeds):
+        r_o, _, _ = O.cpi(*cur, s, C_RESTART, 1e-13)
+        r_o, _, _, _ = O.osp(cur, new, r_o, C_RESTART, 1e-13)
+        assert l1(eng.query(j), r_o) <= 1e-10
+    eng.close()
+
+
 def test_large_batch_in_sub_batches():
     """A batch above osp_max_batch() is merged in sub-batches against the same
     r_old with one propagation: exact OSP of the whole batch. An invalid op in a

@@ -135,3 +135,39 @@ def test_query_slots_api():
         e.topk_wait(0)  # nothing enqueued
     e.query_slots(0)
     e.close()
+
+
+@pytest.mark.parametrize("k", [1, 100, 4096])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_topk_async_many_matches_topk_per_seed(k, normalize):
+    """One launch sequence for many seeds (live seeds, and dead-end seeds whose
+    vector is c e_s, so that the k-th score is a tie among zeros broken by id)
+    gives, slot by slot, the same ids and scores as osp_topk seed by seed."""
+    rng = np.random.default_rng(11)
+    n = 6000
+    src, dst = _graph(rng, n)
+    dead = [7, 8, 9]
+    keep = ~np.isin(src, dead)  # three dead-end nodes
+    src, dst = src[keep], dst[keep]
+    outdeg = np.bincount(src, minlength=n)
+    live = [int(x) for x in rng.choice(np.flatnonzero(outdeg > 0), 37, replace=False)]
+    seeds = live + dead
+    e = _engine(n, src, dst, seeds)
+    e.query_slots(40)
+    order = rng.permutation(len(seeds))
+    for a in range(0, len(seeds), 32):
+        part = [int(x) for x in order[a:a + 32]]
+        slots = list(range(len(part)))
+        e.topk_async_many(slots, part, k, normalize=normalize)
+        for sl, sd in zip(slots, part):
+            ids, sc = e.topk_wait(sl)
+            want_ids, want_sc = e.topk(k, seed_idx=sd, normalize=normalize)
+            assert np.array_equal(ids, want_ids) and np.array_equal(sc, want_sc)
+            r = e.query(sd, normalize=normalize)
+            # the ranking: the k largest scores in order, ties by smaller id
+            ref = np.lexsort((np.arange(n), -r))[:k]
+            assert np.array_equal(ids, ref)
+    with pytest.raises(N.OspError) as err:
+        e.topk_async_many([0, 0], [1, 2], 10)
+    assert err.value.status == N.OSP_EINVAL
+    e.close()

@@ -10,13 +10,15 @@ from paper_1712_00595_gb300 import workloads as W
 
 
 class FakeEngine:
-    """Records the calls the server makes. A top-k answer encodes the number
-    of batches applied when the query was enqueued and the seed it asked for."""
+    """Records the calls the server makes. A top-k answer holds k entries,
+    each id encoding the number of batches applied when the ranking was
+    enqueued and the seed it ranks (version * 1000 + seed)."""
 
     def __init__(self):
         self.batches = []      # op counts of the applied batches
         self.slots = 0
         self.busy = {}         # slot -> (version, seed, k)
+        self.ranked = 0        # seeds ranked
 
     def query_slots(self, k):
         self.slots = k
@@ -29,10 +31,17 @@ class FakeEngine:
     def topk_async(self, slot, k, seed_idx=0):
         assert 0 <= slot < self.slots and slot not in self.busy, "slot in use"
         self.busy[slot] = (len(self.batches), seed_idx, k)
+        self.ranked += 1
+
+    def topk_async_many(self, slots, seeds, k):
+        assert 1 <= len(slots) <= 32 and len(slots) == len(seeds)
+        assert len(set(slots)) == len(slots), "a slot named twice"
+        for sl, sd in zip(slots, seeds):
+            self.topk_async(sl, k, seed_idx=sd)
 
     def topk_wait(self, slot):
         version, seed, k = self.busy.pop(slot)
-        return np.array([version, seed], np.int32), np.array([float(k)])
+        return np.full(k, version * 1000 + seed, np.int32), np.full(k, float(version))
 
 
 def _update(t, tag, size=1):
@@ -74,9 +83,9 @@ def test_ordered_policy_never_merges_past_a_query(seed):
             # it saw exactly the updates that arrived before it
             before = sum(1 for idx in srv.batch_requests[:out.seen] for _ in idx)
             assert before == sum(1 for q in reqs[:i] if isinstance(q, SV.Update))
-            assert [int(ids[1]) for ids, _ in out.topk] == list(r.seeds)
-            assert all(int(ids[0]) == out.seen for ids, _ in out.topk)
-            assert all(float(sc[0]) == r.k for _, sc in out.topk)
+            assert [int(ids[0]) % 1000 for ids, _ in out.topk] == list(r.seeds)
+            assert all(int(ids[0]) // 1000 == out.seen for ids, _ in out.topk)
+            assert all(ids.size == sc.size == r.k for ids, sc in out.topk)
         else:
             assert 0 <= out.batch < len(eng.batches) and i in srv.batch_requests[out.batch]
     assert not eng.busy  # every slot was collected
@@ -94,7 +103,7 @@ def test_latest_policy_merges_every_arrived_update_first():
     for r, out in zip(reqs, res):
         if isinstance(r, SV.Query):
             assert out.seen == len(eng.batches)
-            assert all(int(ids[0]) == len(eng.batches) for ids, _ in out.topk)
+            assert all(int(ids[0]) // 1000 == len(eng.batches) for ids, _ in out.topk)
 
 
 def test_batch_limit_and_oversized_requests():
@@ -115,9 +124,9 @@ def test_slots_are_reused_when_a_query_asks_for_more_seeds_than_slots():
     srv = SV.Server(eng, slots=2, eps=1e-6, policy="ordered")
     q = SV.Query(0.0, (0, 1, 2, 3, 4), 10)
     res = srv.run([_update(0.0, 1), q, _update(0.0, 2), q], realtime=False)
-    assert [int(ids[1]) for ids, _ in res[1].topk] == [0, 1, 2, 3, 4]
-    assert [int(ids[0]) for ids, _ in res[1].topk] == [1] * 5
-    assert [int(ids[0]) for ids, _ in res[3].topk] == [2] * 5
+    assert [int(ids[0]) % 1000 for ids, _ in res[1].topk] == [0, 1, 2, 3, 4]
+    assert [int(ids[0]) // 1000 for ids, _ in res[1].topk] == [1] * 5
+    assert [int(ids[0]) // 1000 for ids, _ in res[3].topk] == [2] * 5
     assert not eng.busy
 
 
@@ -132,3 +141,29 @@ def test_poisson_requests_and_latency_summary():
     summ = SV.latency_summary(res, SV.Query)
     assert summ["count"] == len(qs) and abs(summ["p50_ms"] - 1.0) < 1e-6
     assert SV.latency_summary([], SV.Query) is None
+
+
+@pytest.mark.parametrize("policy", ["ordered", "latest"])
+def test_rankings_reused_within_a_score_version(policy):
+    """Queries for a seed at the same score version (no batch in between) and
+    for no more entries take the ranking already made (or in flight); a larger
+    k or a new version ranks again. Every answer has the requested k entries
+    of the right version and seed."""
+    reqs = [SV.Query(0.0, (0, 1), 10), SV.Query(1.0, (1, 2), 5), SV.Query(2.0, (1,), 20),
+            _update(3.0, 3), SV.Query(4.0, (0, 1), 10), SV.Query(5.0, (0,), 3)]
+    eng = FakeEngine()
+    srv = SV.Server(eng, slots=4, eps=1e-6, policy=policy)
+    res = srv.run(reqs, realtime=False)
+    if policy == "ordered":  # queries see the updates that arrived before them
+        v = [0, 0, 0, None, 1, 1]
+        ranked, reused = 6, 2   # 0, 1, 2, 1 (k = 20) at version 0; 0, 1 at version 1
+    else:  # closed loop: the update is merged first, every query sees version 1
+        v = [1, 1, 1, None, 1, 1]
+        ranked, reused = 4, 4   # 0, 1, 2, 1 (k = 20); the rest reused
+    for i, r in enumerate(reqs):
+        if isinstance(r, SV.Query):
+            got = [(int(ids[0]) % 1000, int(ids[0]) // 1000) for ids, _ in res[i].topk]
+            assert got == [(s, v[i]) for s in r.seeds], (i, got)
+            assert all(ids.size == r.k for ids, _ in res[i].topk)
+    assert eng.ranked == srv.topk_computed == ranked
+    assert srv.topk_reused == reused
