@@ -72,6 +72,7 @@ struct Ctl {
   int multi;                   // 1: several seeds (the Multi block of Dev), 0: one seed
   int n_grp;                   // several seeds: column groups with a running column ...
   int grp[8];                  // ... and their indices, for the next pull step
+  int narrow;                  // bf16 seed block: the next step runs on 4-column rows (see multi.cu)
   double c;
 };
 
@@ -95,6 +96,7 @@ struct Multi {
   double* xacc;        // [nc Sp] offset accumulator
   void* y0; void* y1;  // [nc Sp] gather blocks (double, float or bf16), group-major
   void* e;             // [nc Sp] bf16 rounding residuals of the gather block (bf16 only)
+  void* yn0; void* yn1;  // [nc 4] bf16 narrow gather rows: group slots 0..3 (packed bf16 blocks)
   double* part;        // [kMaxGrid Sp] per-CTA |x| partials
   int* active;         // [Sp] 1 while the column still propagates
   int* touched;        // [Sp] 1: the column has a nonzero offset entry in this call

@@ -1271,6 +1271,8 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     unsigned char* y0 = nullptr;
     unsigned char* y1 = nullptr;
     unsigned char* ebuf = nullptr;
+    unsigned char* yn0 = nullptr;
+    unsigned char* yn1 = nullptr;
     double* hub = nullptr;
     // columns: seeds with out-edges first, then dead-end seeds (whose column
     // has a zero offset unless a batch gives the seed out-edges), each part in
@@ -1302,6 +1304,10 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     ML(y0, cells * ybytes);
     ML(y1, cells * ybytes);
     if (ctx->opt.precision == OSP_PREC_BF16_ACC64) ML(ebuf, cells * 2);
+    if (ctx->opt.precision == OSP_PREC_BF16_ACC64 && K > 1) {  // narrow steps (up to 8 bf16 per node)
+      ML(yn0, (size_t)ctx->nc * 16);
+      ML(yn1, (size_t)ctx->nc * 16);
+    }
     ML(M.part, (size_t)kMaxGrid * 32 * K);
     ML(M.active, 32 * K);
     ML(M.touched, 32 * K);
@@ -1321,6 +1327,8 @@ osp_status osp_set_seeds(osp_ctx* ctx, const int32_t* seeds, int32_t S, double c
     M.y0 = y0;
     M.y1 = y1;
     M.e = ebuf;
+    M.yn0 = yn0;
+    M.yn1 = yn1;
     M.hub_acc = hub;
     // column groups: 32 columns for bf16 gather rows (64-byte slices; measured
     // 8 ms per pass at R-MAT 2^24 against 28.7 ms for one masked 256-column

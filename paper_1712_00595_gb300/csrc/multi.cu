@@ -472,6 +472,269 @@ __device__ __forceinline__ void team_stream(const int* pool, int ll, unsigned of
   flush();
 }
 
+// ---------------------------------------------------------------------------
+// Narrow steps (bf16 rows, packed groups): once the only running columns are
+// group slots 0..W-1 (W = 4 or 8), a step gathers W-value rows (8 or 16
+// bytes) from a compact [node][W] block, whose rows of the nodes with
+// out-edges (ids first in the degree order) mostly stay in L2, instead of the
+// 64-byte slices of the 32-column group. Lane = position of the in-list
+// stream of 32 nodes: each lane loads one row, a segmented warp scan per
+// column sums each node's run, and the run's last lane adds it to the node's
+// sums in shared memory; then lane = node finishes. A step reads the rows the
+// step before it wrote, in that step's layout (the group layout, or a compact
+// block of 8 or 4 columns: W only shrinks within a call).
+// ---------------------------------------------------------------------------
+template <int W>
+struct Narrow {
+  const __nv_bfloat16* src;  // gather rows of the previous step (row u at src + u stride)
+  int stride;                // its row length: 32 (group 0 of the group layout), 8 or 4
+  __nv_bfloat16* dst;        // next compact rows ([node][W])
+  __nv_bfloat16* e;          // residual rows (group 0 of the group layout, slots 0..W-1 used)
+  int col[W];                // columns of R held by slots 0..W-1
+  unsigned act;              // bit c: column col[c] runs
+};
+
+__device__ __forceinline__ void bf16x4(uint2 x, float* f) {
+  f[0] = __uint_as_float(x.x << 16);
+  f[1] = __uint_as_float(x.x & 0xFFFF0000u);
+  f[2] = __uint_as_float(x.y << 16);
+  f[3] = __uint_as_float(x.y & 0xFFFF0000u);
+}
+
+template <int W>
+struct NRow;
+template <>
+struct NRow<4> {
+  uint2 v;
+  __device__ __forceinline__ void load(const __nv_bfloat16* p) {
+    v = __ldcg(reinterpret_cast<const uint2*>(p));
+  }
+  __device__ __forceinline__ void zero() { v = make_uint2(0u, 0u); }
+  __device__ __forceinline__ void unpack(float (&f)[4]) const { bf16x4(v, f); }
+};
+template <>
+struct NRow<8> {
+  uint4 v;
+  __device__ __forceinline__ void load(const __nv_bfloat16* p) {
+    v = __ldcg(reinterpret_cast<const uint4*>(p));
+  }
+  __device__ __forceinline__ void zero() { v = make_uint4(0u, 0u, 0u, 0u); }
+  __device__ __forceinline__ void unpack(float (&f)[8]) const {
+    bf16x4(make_uint2(v.x, v.y), f);
+    bf16x4(make_uint2(v.z, v.w), f + 4);
+  }
+};
+
+__device__ __forceinline__ unsigned pack_bf16x2(float a, float b) {
+  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+         ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Node v's sums x: R += x (running columns), |x| into l1, next compact row and
+// residual w = x s + e_old (when v has out-edges).
+template <int W>
+__device__ __forceinline__ void narrow_finish(const Narrow<W>& N, const Multi& M, int v,
+                                              const float (&x)[W], float s, bool has_in,
+                                              double (&l1)[W]) {
+  if (has_in) {
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      if ((N.act >> c) & 1u) {
+        atomicAdd(M.r + (size_t)v * M.Sp + N.col[c], (double)x[c]);
+        l1[c] += fabs((double)x[c]);
+      }
+  }
+  if (s != 0.f) {
+    __nv_bfloat16* ep = N.e + (size_t)v * 32;
+    NRow<W> eo;
+    eo.load(ep);
+    float e[W], y[W], r[W];
+    eo.unpack(e);
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const float w = x[c] * s + e[c];
+      y[c] = __bfloat162float(__float2bfloat16_rn(w));
+      r[c] = w - y[c];
+    }
+    if constexpr (W == 4) {
+      *reinterpret_cast<uint2*>(N.dst + (size_t)v * 4) =
+          make_uint2(pack_bf16x2(y[0], y[1]), pack_bf16x2(y[2], y[3]));
+      *reinterpret_cast<uint2*>(ep) = make_uint2(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]));
+    } else {
+      *reinterpret_cast<uint4*>(N.dst + (size_t)v * 8) =
+          make_uint4(pack_bf16x2(y[0], y[1]), pack_bf16x2(y[2], y[3]), pack_bf16x2(y[4], y[5]),
+                     pack_bf16x2(y[6], y[7]));
+      *reinterpret_cast<uint4*>(ep) =
+          make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]), pack_bf16x2(r[4], r[5]),
+                     pack_bf16x2(r[6], r[7]));
+    }
+  }
+}
+
+// The in-lists of the nodes [vb, vb + 32) (lane j: list length ll, 0 for
+// lists summed in pieces, at pool offset off) into acc_s[j * W + column]
+// (this warp's shared memory, zeroed by the caller).
+template <int W>
+__device__ __forceinline__ void narrow_stream(const Narrow<W>& N, const int* pool, int ll,
+                                              unsigned off, float* acc_s) {
+  const int lane = threadIdx.x & 31;
+  int incl = ll;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int P = incl - ll;
+  const int E = __shfl_sync(0xffffffffu, incl, 31);
+  constexpr int R = 4;  // windows of 32 positions with their loads in flight together
+  for (int w0 = 0; w0 < E; w0 += 32 * R) {
+    int node[R];
+    NRow<W> row[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int q = w0 + 32 * r + lane;
+      int j = 0;
+#pragma unroll
+      for (int b = 16; b >= 1; b >>= 1) {
+        const int Pc = __shfl_sync(0xffffffffu, P, j + b);
+        if (Pc <= q) j += b;
+      }
+      const int Pj = __shfl_sync(0xffffffffu, P, j);
+      const unsigned oj = __shfl_sync(0xffffffffu, off, j);
+      node[r] = q < E ? j : -1;
+      row[r].zero();
+      if (q < E) row[r].load(N.src + (size_t)__ldg(pool + oj + (unsigned)(q - Pj)) * N.stride);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (w0 + 32 * r >= E) break;  // warp-uniform
+      float v[W];
+      row[r].unpack(v);
+      const int j = node[r];
+      const int prev = __shfl_up_sync(0xffffffffu, j, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != j);
+      const int seg0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+      for (int q = 1; q < 32; q <<= 1) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          const float t = __shfl_up_sync(0xffffffffu, v[c], q);
+          if (lane - q >= seg0) v[c] += t;
+        }
+      }
+      const int nxt = __shfl_down_sync(0xffffffffu, j, 1);
+      if (j >= 0 && (lane == 31 || nxt != j)) {  // one run end per node and window
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc_s[j * W + c] += v[c];
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// One narrow step over the work items (long-list pieces, then tasks).
+template <int W>
+__device__ __forceinline__ void narrow_step(const Dev& d, const Multi& M, Narrow<W>& N, int n_items,
+                                            int n_pieces, int hub_thr, int hub_piece, float* hub_acc,
+                                            float* acc_s, double* my_part, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int Sp = M.Sp;
+  double l1n[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) l1n[c] = 0.0;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&ctl->ctr[1], 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_items) break;
+    if (t < n_pieces) {
+      // a piece of a long in-list; the piece that completes the list finishes it
+      const int h = __ldg(d.piece_hub + t);
+      const int v = __ldg(d.hubs + h);
+      const int piece = t - __ldg(d.hub_pstart + h);
+      const int full = __ldg(d.len_c + v);
+      const int* pl = d.pool_c + __ldg(d.off_c + v) + (unsigned)(piece * hub_piece);
+      const int Lp = min(hub_piece, full - piece * hub_piece);
+      float a[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) a[c] = 0.f;
+      for (int b = 0; b < Lp; b += 128) {
+        NRow<W> rw[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = b + 32 * r + lane;
+          rw[r].zero();
+          if (e < Lp) rw[r].load(N.src + (size_t)__ldg(pl + e) * N.stride);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float f[W];
+          rw[r].unpack(f);
+#pragma unroll
+          for (int c = 0; c < W; ++c) a[c] += f[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c) a[c] = warp_sum(a[c]);
+      float* ha = hub_acc + (size_t)h * Sp;  // group slots 0..W-1
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < W; ++c)
+          if ((N.act >> c) & 1u) atomicAdd(ha + c, a[c]);
+        __threadfence();
+        const int np = (full + hub_piece - 1) / hub_piece;
+        if (atomicAdd(&M.hub_cnt[h * 8], 1) == np - 1) {
+          __threadfence();
+          float x[W];
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            x[c] = __ldcg(ha + c);
+            ha[c] = 0.f;
+          }
+          M.hub_cnt[h * 8] = 0;
+          narrow_finish<W>(N, M, v, x, scale_of<float>(d, v), true, l1n);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    const int task = t - n_pieces;
+    const int c0t = __ldg(d.task_first + task), c1t = __ldg(d.task_first + task + 1);
+    for (int vb = c0t; vb < c1t; vb += 32) {
+      const int vl = vb + lane;
+      int len = 0;
+      unsigned off = 0;
+      float sc = 0.f;
+      if (vl < c1t) {
+        len = __ldg(d.len_c + vl);
+        off = __ldg(d.off_c + vl);
+        sc = scale_of<float>(d, vl);
+      }
+      const bool mine = vl < c1t && len <= hub_thr;  // hubs go by pieces
+      const bool fin = mine && (len > 0 || sc != 0.f);
+      if (!__ballot_sync(0xffffffffu, fin)) continue;
+#pragma unroll
+      for (int c = 0; c < W; c += 4)
+        reinterpret_cast<float4*>(acc_s)[(lane * W + c) / 4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+      narrow_stream<W>(N, d.pool_c, mine ? len : 0, off, acc_s);
+      __syncwarp();
+      if (fin) {
+        float x[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) x[c] = acc_s[lane * W + c];
+        narrow_finish<W>(N, M, vl, x, sc, len > 0, l1n);
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const double sum = warp_sum(l1n[c]);
+    if (lane == 0 && ((N.act >> c) & 1u)) my_part[N.col[c]] += sum;
+  }
+}
+
 // 16-byte asynchronous copy global -> shared (L2 only), and the wait for this
 // thread's copies.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -497,7 +760,11 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
   __shared__ double s_sum[kPropThreads];
   __shared__ double s_key[kMaxSeeds];
   __shared__ unsigned s_gmask;
-  if (threadIdx.x == 0) s_gmask = 0;
+  __shared__ int s_maxslot;
+  if (threadIdx.x == 0) {
+    s_gmask = 0;
+    s_maxslot = -1;
+  }
   const bool pack = M.pack != 0 && KG == 1;
   // thread t sums column t % Sp over the CTAs b = t / Sp (mod Q) with eight
   // independent accumulators; the Q slices are then added in a fixed order
@@ -557,7 +824,9 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
         M.res_bound[j] += (1.0 - ctl->c) * L;
       } else {
         live = 1;
-        atomicOr(&s_gmask, 1u << ((pack ? __ldcg(M.col_slot + j) : j) / G));
+        const int slot = pack ? __ldcg(M.col_slot + j) : j;
+        atomicOr(&s_gmask, 1u << (slot / G));
+        atomicMax(&s_maxslot, slot);
       }
     }
   }
@@ -576,7 +845,10 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
       }
       M.slot_col[rank] = j;
       M.col_slot[j] = rank;
-      if (kj >= 0.0) atomicOr(&s_gmask, 1u << (rank / G));
+      if (kj >= 0.0) {
+        atomicOr(&s_gmask, 1u << (rank / G));
+        atomicMax(&s_maxslot, rank);
+      }
     }
   }
   seen = warp_max(seen);
@@ -604,6 +876,11 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
     for (int g = 0; g < 8; ++g)
       if (s_gmask & (1u << g)) ctl->grp[ng++] = g;
     ctl->n_grp = ng;
+    // packed bf16 groups with only slots 0..7 (0..3) running: narrow steps of
+    // 8 (4) columns from now on
+    ctl->narrow = pack && M.yn0 != nullptr && ng == 1 && ctl->grp[0] == 0 && s_maxslot < 8
+                      ? (s_maxslot < 4 ? 4 : 8)
+                      : 0;
     ctl->stop = !any;
     for (int i = 0; i < 4; ++i) ctl->ctr[i] = 0;
   }
@@ -1191,6 +1468,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   }
 
   A* hub_acc = (A*)M.hub_acc;
+  int prev_narrow = 0;  // row width of the compact block the last step wrote (0: none)
   for (int it = 1;; ++it) {
     if (*(volatile int*)&ctl->stop) break;
     if (threadIdx.x < 8) s_grp[threadIdx.x] = *(volatile int*)&ctl->grp[threadIdx.x];
@@ -1217,6 +1495,38 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
         }
       }
     };
+    int narrow = 0;  // row width of a narrow step (0: a step over column groups)
+    if constexpr (kTeam) narrow = *(volatile int*)&ctl->narrow;
+    if constexpr (kTeam) {
+      if (narrow) {
+        __nv_bfloat16* yn[2] = {(__nv_bfloat16*)M.yn0, (__nv_bfloat16*)M.yn1};
+        const __nv_bfloat16* src =
+            prev_narrow ? yn[(it - 1) & 1] : reinterpret_cast<const __nv_bfloat16*>(ys);
+        const int stride = prev_narrow ? prev_narrow : 32;
+        float* acc_s = s_team_acc + wid * 1024;
+        if (narrow == 4) {
+          Narrow<4> N{src, stride, yn[it & 1], reinterpret_cast<__nv_bfloat16*>(eb), {}, 0u};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            N.col[c] = __ldcg(M.slot_col + c);
+            if (*(volatile int*)&M.active[N.col[c]]) N.act |= 1u << c;
+          }
+          narrow_step<4>(d, M, N, n_items, n_pieces, hub_thr, hub_piece, (float*)hub_acc, acc_s,
+                         my_part, ctl);
+        } else {
+          Narrow<8> N{src, stride, yn[it & 1], reinterpret_cast<__nv_bfloat16*>(eb), {}, 0u};
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            N.col[c] = __ldcg(M.slot_col + c);
+            if (*(volatile int*)&M.active[N.col[c]]) N.act |= 1u << c;
+          }
+          narrow_step<8>(d, M, N, n_items, n_pieces, hub_thr, hub_piece, (float*)hub_acc, acc_s,
+                         my_part, ctl);
+        }
+      }
+    }
+    prev_narrow = narrow;
+    if (!narrow)
     for (;;) {
       int t = 0;
       if (lane == 0) t = atomicAdd(&ctl->ctr[1], 1);
