@@ -605,8 +605,9 @@ def run_multi(args, rank, world, name=None, steps=None, warmup=None, extras=True
                        and S > 32 and args.seed_group in (0, 32) else "fixed"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "traffic_per_alg_byte": float(rec["dram_bytes_per_alg_byte"]) if rec else None,
-                     "traffic_source": rec.get("source") if rec else None,
+                     "traffic_per_alg_byte": float(rec["dram_bytes_per_alg_byte"])
+                     if traffic is not None else None,
+                     "traffic_source": rec.get("source") if traffic is not None else None,
                      "kernel": "k_propagate_multi", "peak_kind": peak_kind + " (hbm_gbs copy)",
                      "alg_bytes_per_launch": ab / K, "ms_per_launch": prop_ms / K,
                      "dense_step_alg_bytes": dense_step},
