@@ -731,7 +731,7 @@ __device__ __forceinline__ void narrow_step(const Dev& d, const Multi& M, Narrow
 #pragma unroll
   for (int c = 0; c < W; ++c) {
     const double sum = warp_sum(l1n[c]);
-    if (lane == 0 && ((N.act >> c) & 1u)) my_part[N.col[c]] += sum;
+    if (lane == 0 && ((N.act >> c) & 1u)) atomicAdd(my_part + N.col[c], sum);
   }
 }
 
@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   __shared__ float s_team_acc[kTeam ? kPropWarps * 1024 : 1];                 // node x column sums
   __shared__ __align__(16) __nv_bfloat16 s_team_e[kTeam ? kPropWarps * 1024 : 8];  // residual rows
   __shared__ BarShared sh;
-  __shared__ double s_part[kPropWarps * kMaxSeeds];  // per warp, per column |x| sums
+  __shared__ double s_part[kMaxSeeds];  // per column |x| sums of the CTA (shared-memory atomics)
   __shared__ int s_grp[8];
   __shared__ int s_ngrp;
   __shared__ unsigned s_tmask;
@@ -1306,7 +1306,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  double* my_part = s_part + wid * kMaxSeeds;
+  double* my_part = s_part;
   if (blockIdx.x == 0 && threadIdx.x == 0) d.step_ns[0] = global_ns();
 
   // per-CTA column sums of the warps' partials (fixed order) into M.part
@@ -1314,7 +1314,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
     __syncthreads();
     for (int j = threadIdx.x; j < Sp; j += blockDim.x) {
       double a = 0.0;
-      for (int i = 0; i < kPropWarps; ++i) a += s_part[i * kMaxSeeds + j];
+      a = s_part[j];
       M.part[(size_t)blockIdx.x * Sp + j] = a;
     }
     __threadfence();
@@ -1340,7 +1340,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
         stamped &= stamped - 1;
         for (unsigned t = tb; t; t &= t - 1) {
           const int j = lane + 32 * (__ffs(t) - 1);
-          my_part[j] += fabs(__ldcg(M.xacc + (size_t)v * Sp + j));
+          atomicAdd(my_part + j, fabs(__ldcg(M.xacc + (size_t)v * Sp + j)));
         }
       }
     }
@@ -1440,7 +1440,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
 #pragma unroll
             for (int k = 0; k < KG; ++k) {
               rr[k] += x[k];
-              my_part[g * G + lane * KG + k] += fabs(x[k]);
+              atomicAdd(my_part + g * G + lane * KG + k, fabs(x[k]));
               z[k] = 0.0;
               const A w = (A)((A)x[k] * s);
               yv[k] = from_acc(w, (TY*)nullptr);
@@ -1490,7 +1490,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       if (cur >= 0) {
 #pragma unroll
         for (int k = 0; k < KG; ++k) {
-          my_part[(kTeam && pack ? pcol : cur * G + lane * KG) + k] += l1[k];
+          atomicAdd(my_part + (kTeam && pack ? pcol : cur * G + lane * KG) + k, l1[k]);
           l1[k] = 0.0;
         }
       }
