@@ -750,15 +750,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // the history entry (max over the columns that ran the step). A column whose
 // x(0) is exactly zero has only zero terms: under the eps rule its one
 // do-while step is counted and it stops at once.
+// s_sum (kPropThreads doubles) and s_key (kMaxSeeds doubles) are shared-memory
+// scratch of the caller (buffers that are idle at the grid barrier).
 template <int KG>
-__device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long long m) {
+__device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long long m, double* s_sum,
+                             double* s_key) {
   constexpr int G = 32 * KG;
   const Multi& M = d.mu;
   const int Sp = M.Sp;
   Ctl* ctl = d.ctl;
   __shared__ double s_max[kPropThreads / 32];
-  __shared__ double s_sum[kPropThreads];
-  __shared__ double s_key[kMaxSeeds];
   __shared__ unsigned s_gmask;
   __shared__ int s_maxslot;
   if (threadIdx.x == 0) {
@@ -1259,10 +1260,13 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
   // bf16 rows of 32-column groups are gathered by teams of 8 lanes over a flat
   // edge stream (team_stream / team_piece); the other forms walk node by node
   constexpr bool kTeam = std::is_same<TY, __nv_bfloat16>::value && KG == 1 && !kBulk;
-  __shared__ float s_team_acc[kTeam ? kPropWarps * 1024 : 1];                 // node x column sums
+  __shared__ __align__(16) float s_team_acc[kTeam ? kPropWarps * 1024 : 1];  // node x column sums
   __shared__ __align__(16) __nv_bfloat16 s_team_e[kTeam ? kPropWarps * 1024 : 8];  // residual rows
   __shared__ BarShared sh;
   __shared__ double s_part[kMaxSeeds];  // per column |x| sums of the CTA (shared-memory atomics)
+  // the decision's scratch: the team node sums (idle at the grid barrier), else its own
+  __shared__ double s_dec_own[kTeam ? 1 : kPropThreads + kMaxSeeds];
+  double* s_dec = kTeam ? reinterpret_cast<double*>(s_team_acc) : s_dec_own;
   __shared__ int s_grp[8];
   __shared__ int s_ngrp;
   __shared__ unsigned s_tmask;
@@ -1345,7 +1349,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       }
     }
     column_sums();
-    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, 0, m);
+    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, 0, m, s_dec, s_dec + kPropThreads);
     if (!bar_release(ctl, sh)) return;
     // 2. R += x(0) and the y(0) rows, in group slots
     if (threadIdx.x < 8) s_grp[threadIdx.x] = *(volatile int*)&ctl->grp[threadIdx.x];
@@ -1463,7 +1467,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       }
     }
     column_sums();
-    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, 0, m);
+    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, 0, m, s_dec, s_dec + kPropThreads);
     if (!bar_release(ctl, sh)) return;
   }
 
@@ -1878,7 +1882,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
     }
     flush();
     column_sums();
-    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, it, m);
+    if (bar_arrive(ctl, sh)) decide_multi<KG>(d, pp, it, m, s_dec, s_dec + kPropThreads);
     if (!bar_release(ctl, sh)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->epoch = epoch + 1;
