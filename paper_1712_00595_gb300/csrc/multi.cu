@@ -1139,7 +1139,9 @@ __global__ void __launch_bounds__(1024) k_offset_multi_plan(Dev d) {
 
 // Warp per offset item: R_old[u] times -(1-c)/d_u into xacc over the old
 // out-list entries, times +(1-c)/d'_u over the new ones (one combined term
-// for an entry in both lists); stamps the targets.
+// for an entry in both lists); stamps the targets. Lane l owns columns
+// l, l + 32, ..., so each atomic instruction of the warp covers 32
+// consecutive columns (8 sectors) of the target's row.
 template <int K>
 __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
   constexpr int Sp = 32 * K;
@@ -1157,8 +1159,9 @@ __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
     const int q = p - d.rec_pstart[c];
     const int u = d.rec_r_node[c];
     const int L = d.rec_old_len[c], dp = d.rec_dp[c];
-    alignas(16) double ru[K];
-    load_cg(d.mu.r + (size_t)u * Sp + lane * K, ru);
+    double ru[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) ru[k] = __ldcg(d.mu.r + (size_t)u * Sp + lane + 32 * k);
     bool nz = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) nz |= ru[k] != 0.0;
@@ -1189,11 +1192,11 @@ __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
         const double wj = __shfl_sync(0xffffffffu, wgt, j);
         if (wj == 0.0) continue;  // warp-uniform
         const int aj = __shfl_sync(0xffffffffu, a, j);
-        double* row = d.mu.xacc + (size_t)aj * Sp + lane * K;
+        double* row = d.mu.xacc + (size_t)aj * Sp + lane;
 #pragma unroll
         for (int k = 0; k < K; ++k)
           if (ru[k] != 0.0) {
-            atomicAdd(row + k, wj * ru[k]);
+            atomicAdd(row + 32 * k, wj * ru[k]);
             hit |= 1u << k;
           }
         if (lane == 0) d.mark[aj] = epoch;
@@ -1204,7 +1207,7 @@ __global__ void __launch_bounds__(256) k_offset_multi(Dev d) {
   // have x(i) = 0 for every i)
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (hit & (1u << k)) d.mu.touched[lane * K + k] = 1;
+    if (hit & (1u << k)) d.mu.touched[lane + 32 * k] = 1;
 }
 
 // CPI start for every column: x(0) = c e_{s_j} in column j.
