@@ -128,7 +128,11 @@ typedef struct {
                             group). A pull step walks the graph
                             once per group that still has a running column, so groups whose
                             seeds have all stopped cost nothing; inside a group, a lane whose
-                            columns have all stopped loads and stores nothing. */
+                            columns have all stopped loads and stores nothing. With bf16 rows
+                            in 32-column groups (and more than 32 seeds) each call also orders
+                            the columns into groups by offset size, largest first, and once
+                            only the first 8 (4) of that order run, steps read compact 8 (4)
+                            column rows. Results are the same up to rounding order. */
     int32_t deterministic; /* != 0 (one seed; osp_set_seeds with two or more returns
                               OSP_ENOTSUP): every propagation step pulls (no push steps, so
                               each costs a pass over all edges), warps take their work in a
