@@ -821,8 +821,10 @@ __device__ void decide_multi(const Dev& d, const PropParams& pp, int it, long lo
       }
       if (stop) {
         M.active[j] = 0;
-        // the untaken tail's residual x(k+1) has norm <= (1-c) ||x(k)||_1
-        M.res_bound[j] += (1.0 - ctl->c) * L;
+        // the untaken tail's residual x(k+1) has norm <= (1-c) ||x(k)||_1; L may
+        // hold float sums of at most 32 nonnegative terms (relative error below
+        // 2^-19), hence the margin
+        M.res_bound[j] += (1.0 - ctl->c) * L * (1.0 + 0x1p-18);
       } else {
         live = 1;
         const int slot = pack ? __ldcg(M.col_slot + j) : j;
@@ -1687,7 +1689,9 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
           team_stream(d.pool_c, mine ? my_len : 0, my_off, ysg, on4, pol, cold, hot_n, acc_s);
           cp_async_wait_all();
           __syncwarp();
-          // finish: lane = column
+          // finish: lane = column; |x| of the run summed in float (at most 32
+          // nonnegative terms), then added to the FP64 partial once
+          float l1f = 0.f;
           for (unsigned fb = fin; fb; fb &= fb - 1) {
             const int j = __ffs(fb) - 1;
             const int v = vb + j;
@@ -1697,7 +1701,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
             const float x = acc_s[j * 32 + lane];
             if (has_in) {
               atomicAdd(M.r + rbase_of(v), (double)x);
-              l1[0] += fabs((double)x);
+              l1f += fabsf(x);
             }
             if (sj != 0.f) {
               const float w = x * sj + __bfloat162float(e_s[j * 32 + lane]);
@@ -1706,6 +1710,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
               eb[ybase_of(v)] = __float2bfloat16_rn(w - __bfloat162float(yv));
             }
           }
+          l1[0] += (double)l1f;
           __syncwarp();
         }
         continue;
