@@ -1247,10 +1247,11 @@ struct MultiOcc {
 
 // The seed block, one persistent cooperative launch per call: the x(0) pass
 // and every pull step. Columns are processed in groups of G = 32 KG (lane l
-// owns columns [KG l, KG l + KG) of the group); a pull step walks its work
-// items once per group that still has a running column, group after group,
-// so the gathered rows of one group share L2 while it is walked, and groups
-// whose columns have all stopped cost nothing. The gather blocks (and the
+// owns columns [KG l, KG l + KG) of the group); a pull step runs each work
+// item once per group that still has a running column (an item's groups one
+// after the other, so its ids are read from DRAM once; the groups share the
+// L2 budget for hot rows), and groups whose columns have all stopped cost
+// nothing. The gather blocks (and the
 // bf16 residuals) are laid out group-major, [group][node][G], so that a
 // group's row is one contiguous slice of G elements; R is [node][Sp].
 // kBulk: in-lists stage their source rows in shared memory by bulk
@@ -1488,6 +1489,9 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
     TY* yd = yb[it & 1];
     const int n_items = n_pieces + n_tasks;
     const long long total = (long long)s_ngrp * n_items;
+    // the groups of a step are gathered side by side: they share the L2
+    // budget for hot rows
+    const int hot_step = s_ngrp > 1 ? hot_n / s_ngrp : hot_n;
     int cur = -1;  // column group of the items this warp works on now
     int pcol = -1;  // packed bf16 groups: this lane's column in group cur
     unsigned act = 0;
@@ -1541,8 +1545,10 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
       if (lane == 0) t = atomicAdd(&ctl->ctr[1], 1);
       t = __shfl_sync(0xffffffffu, t, 0);
       if (t >= total) break;
-      const int gi = t / n_items;
-      const int ti = t - gi * n_items;
+      // task-major: a work item's groups come one after the other, so its
+      // in-list ids and node headers are read from DRAM once for all groups
+      const int gi = t % s_ngrp;
+      const int ti = t / s_ngrp;
       const int g = s_grp[gi];
       if (g != cur) {
         flush();
@@ -1575,7 +1581,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
         const int L = min(hub_piece, full - piece * hub_piece);
         if constexpr (kTeam) {
           float a4[4];
-          team_piece(p, L, ysg, on4, pol, cold, hot_n, a4);
+          team_piece(p, L, ysg, on4, pol, cold, hot_step, a4);
           float* ha4 = (float*)hub_acc + (size_t)h * Sp + (size_t)g * G + 4 * lane;
           if (lane < 8 && on4) {
 #pragma unroll
@@ -1686,7 +1692,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
           for (int q = 0; q < 8; ++q)
             reinterpret_cast<float4*>(acc_s)[lane + 32 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
           __syncwarp();
-          team_stream(d.pool_c, mine ? my_len : 0, my_off, ysg, on4, pol, cold, hot_n, acc_s);
+          team_stream(d.pool_c, mine ? my_len : 0, my_off, ysg, on4, pol, cold, hot_step, acc_s);
           cp_async_wait_all();
           __syncwarp();
           // finish: lane = column; |x| of the run summed in float (at most 32
