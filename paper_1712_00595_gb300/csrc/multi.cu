@@ -586,9 +586,9 @@ __device__ __forceinline__ void narrow_stream(const Narrow<W>& N, const int* poo
   }
   const int P = incl - ll;
   const int E = __shfl_sync(0xffffffffu, incl, 31);
-  // windows of 32 positions with their loads in flight together (8-byte rows
-  // leave registers for twice as many)
-  constexpr int R = W == 4 ? 8 : 4;
+  // windows of 32 positions with their loads in flight together (narrower
+  // rows leave registers for more)
+  constexpr int R = W == 4 ? 8 : 6;
   for (int w0 = 0; w0 < E; w0 += 32 * R) {
     int node[R];
     NRow<W> row[R];
