@@ -726,6 +726,22 @@ def cpu_baseline(args, n, src, dst, seed, stream):
             "cpi_from_scratch": {"ms": 1e3 * dt_cpi, "iterations": int(cst["iterations"])}}
 
 
+def l1_lookup_roofline(stats, prop_ms, clk, device):
+    """Gathers per second of the one-seed propagation against one L1 sector
+    lookup per SM cycle (SM count and the median SM clock sampled during the
+    timed region)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    lookups = float(sum(s["visited_edges"] for s in stats))
+    achieved = lookups / (prop_ms / 1e3) / 1e9
+    peak = sms * mhz * 1e6 / 1e9
+    return {"bound": "l1 lookups", "achieved": achieved, "peak": peak, "unit": "G lookups/s",
+            "frac": achieved / peak, "basis": "one random 4-byte gather per visited edge, one "
+            "32-byte sector lookup per SM cycle (%d SMs at %.0f MHz)" % (sms, mhz)}
+
+
 def run_ours(args, rank, world, steps=None, warmup=None, extras=True):
     import torch
 
@@ -826,6 +842,10 @@ def run_ours(args, rank, world, steps=None, warmup=None, extras=True):
                      "frac": achieved / peak, "traffic": traffic_from_profile(),
                      "kernel": "k_propagate<float>", "peak_kind": peak_kind + " (hbm_gbs copy)",
                      "alg_bytes_per_launch": ab / K, "ms_per_launch": prop_ms / K},
+        # the working set of this kernel lives in L2; its ceiling is the rate of
+        # the random 4-byte gathers (one per visited edge), each a 32-byte sector
+        # lookup in L1, at one lookup per SM cycle
+        "roofline_l1": l1_lookup_roofline(stats, prop_ms, clk, local),
         "phases_ms_per_step": {"update_merge_offset": upd_ms / K, "propagation": prop_ms / K},
         "batch_ms": {"median": float(np.median(ms)), "p99": float(np.percentile(ms, 99)),
                      "max": float(max(ms))},
@@ -1070,7 +1090,7 @@ def run_growshrink(args, rank, world, steps=32):
 def summary(line, keys=("value", "unit", "ms_per_step", "steps", "warmup")):
     """A nested benchmark's main figures."""
     out = {k: line.get(k) for k in keys if k in line}
-    for k in ("roofline", "l1_vs_fp64", "e2e", "cpu_baseline", "fp64_path", "latency",
+    for k in ("roofline", "roofline_l1", "l1_vs_fp64", "e2e", "cpu_baseline", "fp64_path", "latency",
               "iterations_per_step", "column_steps_per_batch", "phases_ms_per_step", "config",
               "gpu_launches", "push_iterations_per_step", "engine_batches", "offered_seconds",
               "served_seconds", "clocks"):
