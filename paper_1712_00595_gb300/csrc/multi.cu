@@ -90,6 +90,13 @@ struct L2Pol {
   unsigned long long normal;  // evict_normal
 };
 
+// R += x without a return value, the line marked evict-first in L2: score rows
+// are touched once per step and should not push gathered rows out of L2.
+__device__ __forceinline__ void red_add_once(double* p, double x, unsigned long long pol) {
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(x), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ L2Pol make_l2pol() {
   L2Pol p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
@@ -1604,7 +1611,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
             if (lane == 0) M.hub_cnt[h * 8 + g] = 0;
             const float sv = scale_of<float>(d, v);
             if (act) {
-              atomicAdd(M.r + rbase_of(v), (double)x);
+              red_add_once(M.r + rbase_of(v), (double)x, pol.once);
               l1[0] += fabs((double)x);
               if (sv != 0.f) {
                 const float w = x * sv + __bfloat162float(eb[ybase_of(v)]);
@@ -1708,7 +1715,7 @@ __global__ void __launch_bounds__(kPropThreads, MultiOcc<TY, KG>::value)
             if (!act) continue;
             const float x = acc_s[j * 32 + lane];
             if (has_in) {
-              atomicAdd(M.r + rbase_of(v), (double)x);
+              red_add_once(M.r + rbase_of(v), (double)x, pol.once);
               l1f += fabsf(x);
             }
             if (sj != 0.f) {
