@@ -726,13 +726,10 @@ def cpu_baseline(args, n, src, dst, seed, stream):
             "cpi_from_scratch": {"ms": 1e3 * dt_cpi, "iterations": int(cst["iterations"])}}
 
 
-def l1_lookup_roofline(stats, prop_ms, clk, device):
+def l1_lookup_roofline(stats, prop_ms, clk, sms):
     """Gathers per second of the one-seed propagation against one L1 sector
-    lookup per SM cycle (SM count and the median SM clock sampled during the
+    lookup per SM cycle (sms SMs at the median SM clock sampled during the
     timed region)."""
-    import torch
-
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     lookups = float(sum(s["visited_edges"] for s in stats))
     achieved = lookups / (prop_ms / 1e3) / 1e9
@@ -845,7 +842,8 @@ def run_ours(args, rank, world, steps=None, warmup=None, extras=True):
         # the working set of this kernel lives in L2; its ceiling is the rate of
         # the random 4-byte gathers (one per visited edge), each a 32-byte sector
         # lookup in L1, at one lookup per SM cycle
-        "roofline_l1": l1_lookup_roofline(stats, prop_ms, clk, local),
+        "roofline_l1": l1_lookup_roofline(
+            stats, prop_ms, clk, torch.cuda.get_device_properties(local).multi_processor_count),
         "phases_ms_per_step": {"update_merge_offset": upd_ms / K, "propagation": prop_ms / K},
         "batch_ms": {"median": float(np.median(ms)), "p99": float(np.percentile(ms, 99)),
                      "max": float(max(ms))},

@@ -102,3 +102,13 @@ def test_traffic_record_is_ignored_when_the_kernel_changed(monkeypatch):
         assert rec > 1e8
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16 if cur != "0" * 16 else "1")
     assert bench.traffic_from_profile() is None
+
+
+def test_l1_lookup_roofline():
+    """One gather per visited edge against one sector lookup per SM cycle."""
+    stats = [{"visited_edges": 16_000_000}, {"visited_edges": 48_000_000}]
+    r = bench.l1_lookup_roofline(stats, prop_ms=0.4, clk={"sm_mhz": 2000.0}, sms=150)
+    assert r["achieved"] == pytest.approx(64e6 / 0.4e-3 / 1e9)   # G lookups/s
+    assert r["peak"] == pytest.approx(150 * 2.0)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert bench.l1_lookup_roofline(stats, 0.4, None, 150)["peak"] == pytest.approx(150 * 2.07)
