@@ -39,7 +39,8 @@ typedef struct osp_ctx osp_ctx; /* opaque; created by osp_create, owned by the l
 typedef enum {
     OSP_OK = 0,
     OSP_EINVAL = -1,   /* bad argument or invalid update batch; state unchanged */
-    OSP_ENOMEM = -2,   /* device allocation failed */
+    OSP_ENOMEM = -2,   /* device allocation failed, the HBM budget would be exceeded, or the
+                          node or edge capacity reserved at load is exhausted */
     OSP_ECUDA = -3,    /* a CUDA runtime call failed */
     OSP_ETIMEOUT = -4, /* a bounded device wait (grid barrier) gave up */
     OSP_ENOCONV = -5,  /* iteration cap reached before ||x(i)||_1 <= eps; scores hold the
